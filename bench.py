@@ -1,0 +1,429 @@
+"""Benchmark of the coupled IBM-LBM time step on GB300.
+
+Default workload (N = 1): 256^3 D3Q19 lattice, tube of radius 120 along x
+with bounce-back walls, body-force drive (centreline Re ~ 1), 3000
+biconcave red-cell membranes of 642 vertices (diameter 16 lu), FP32
+population storage. One "step" = one coupled time step (marker forces,
+spreading, collide-stream, interpolation + advection).
+
+Prints ONE JSON line (rank 0):
+  value        lattice updates per second over the whole box (MLUPS), inputs
+               resident in HBM, device time (CUDA events), max over ranks
+  e2e          same metric through the C ABI with host buffers: upload of the
+               lattice state and markers, K steps, download of fields and
+               markers inside the timed region
+  roofline     the collide-stream kernel (the dominant one): algorithmic bytes
+               per launch / its average event-timed duration, against the
+               measured HBM copy bandwidth
+  cpu_baseline the FP64 oracle as it stands, one full coupled step of the
+               same workload on one host core
+With --gpus N > 1 (launched under torchrun) every rank runs an independent
+replica of the workload on its own GPU: the path has no exchange step, so
+there is no collective on the data path ("scaling": "weak").
+``--impl reference`` times the oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = 'coupled IBM-LBM MLUPS & % of HBM roofline (1 GB300); batched p50/p99 latency'
+UNIT = 'MLUPS'
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+def make_workload(name: str):
+    from paper_1704_04551_gb300 import inputs as I
+    if name in ('tube256', 'tube256_f16', 'tube256_bf16'):
+        w = I.rbc_tube(n=256, radius=120.0, n_cells=3000, seed=1706, steps=2000)
+        w['storage'] = {'tube256': 'f32', 'tube256_f16': 'f16', 'tube256_bf16': 'bf16'}[name]
+        w['label'] = f'rbc_tube_256^3_R120_3000x642_{w["storage"]}'
+        return w
+    if name == 'tube64':
+        w = I.rbc_tube(n=64, radius=30.0, n_cells=50, seed=1707, steps=1000)
+        w['storage'] = 'f32'
+        w['label'] = 'rbc_tube_64^3_R30_50x642_f32'
+        return w
+    if name == 'shear32':
+        w = I.shear_ellipsoid(n=32, steps=500)
+        w['storage'] = 'f32'
+        w['label'] = 'rigid_ellipsoid_shear_32^3_f32'
+        return w
+    raise ValueError(name)
+
+
+def fluid_cells(lat):
+    nx, ny, nz = lat['nx'], lat['ny'], lat['nz']
+    if lat['geometry'] != 2:
+        return nx * ny * nz
+    y, z = np.meshgrid(np.arange(ny), np.arange(nz), indexing='ij')
+    yc, zc = (ny - 1) / 2, (nz - 1) / 2
+    R2 = np.float32(lat['tube_radius'] ** 2)
+    dy = (y - yc).astype(np.float32)
+    dz = (z - zc).astype(np.float32)
+    return int(nx * np.count_nonzero(~(dy * dy + dz * dz > R2)))
+
+
+def touched_cells(lat, X):
+    """Fluid cells inside the 4^3 delta stencil of at least one marker."""
+    nx, ny, nz = lat['nx'], lat['ny'], lat['nz']
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    base = np.floor(X).astype(np.int64) - 1
+    for c in range(4):
+        z = base[2] + c
+        for b in range(4):
+            y = base[1] + b
+            for a in range(4):
+                x = np.mod(base[0] + a, nx)
+                if lat['geometry'] == 0:
+                    yy, zz, ok = np.mod(y, ny), np.mod(z, nz), slice(None)
+                    mask[zz, yy, x] = True
+                    continue
+                if lat['geometry'] == 1:
+                    zz = np.mod(z, nz)
+                    ok = (y >= 0) & (y < ny)
+                    mask[zz[ok], y[ok], x[ok]] = True
+                else:
+                    ok = (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+                    mask[z[ok], y[ok], x[ok]] = True
+    if lat['geometry'] == 2:
+        zz, yy = np.meshgrid(np.arange(nz), np.arange(ny), indexing='ij')
+        dy = (yy - (ny - 1) / 2).astype(np.float32)
+        dz = (zz - (nz - 1) / 2).astype(np.float32)
+        solid = dy * dy + dz * dz > np.float32(lat['tube_radius'] ** 2)
+        mask &= ~solid[:, :, None]
+    return int(mask.sum())
+
+
+def bytes_per_pop(storage):
+    return 4 if storage == 'f32' else 2
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.dev), f'--query-gpu={self.Q}',
+                                          '--format=csv,noheader,nounits', '-lms', '100'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=['nvidia-smi unavailable'], samples=0)
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(',')]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == 'active':
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d['hbm_gbs']), 'measured'
+    return 6800.0, 'fallback'
+
+
+def collide_traffic(storage):
+    """DRAM bytes per collide launch from the committed ncu summary, if the
+    kernel source is unchanged since it was taken."""
+    src = os.path.join(ROOT, 'paper_1704_04551_gb300', 'csrc', 'lbm.cu')
+    sha = hashlib.sha256(open(src, 'rb').read()).hexdigest()[:16]
+    p = os.path.join(ROOT, 'profiles', f'collide_tube256_{storage}.md')
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ':' in line and line.startswith('- '):
+            k, v = line[2:].split(':', 1)
+            vals[k.strip()] = v.strip().strip('`')
+    if vals.get('lbm.cu sha256[:16]') != sha:
+        return None
+    try:
+        return float(vals['dram bytes per launch (full size)'])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ----------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault('MASTER_ADDR', '127.0.0.1')
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def reduce_max(dist, value, device='cpu'):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(units_per_rank, max_seconds, n_ranks):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    return units_per_rank * n_ranks / max_seconds
+
+
+# ----------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle as it stands
+# ----------------------------------------------------------------------------
+def time_oracle(w, steps, warmup=0):
+    import oracle as O
+    t0 = time.perf_counter()
+    o = O.Oracle.from_workload(w)
+    setup = time.perf_counter() - t0
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    N = w['lattice']['nx'] * w['lattice']['ny'] * w['lattice']['nz']
+    return dict(mlups=N * steps / dt / 1e6, seconds=dt, setup_s=setup, steps=steps)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload)
+    # each requested step is bounded: at most a couple of full oracle steps
+    # are timed so that the whole run ends within a few minutes
+    n = max(1, min(args.steps, args.ref_max_steps))
+    r = time_oracle(w, n, warmup=min(args.warmup, 0))
+    line = dict(impl='reference', metric=METRIC, value=r['mlups'], unit=UNIT, n_gpus=args.gpus, steps=n,
+                warmup=0, ms_per_step=1e3 * r['seconds'] / n, higher_is_better=True, scaling='weak',
+                vs_baseline=None, dtype='f64', data='synthetic',
+                config=dict(workload=w['label'], requested_steps=args.steps, lattice=[w['lattice'][k] for k in ('nx', 'ny', 'nz')],
+                            markers=int(w['X'].shape[1]), bodies=len(w['bodies'])),
+                cpu_baseline=dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
+                                  sample=f'{n} full coupled step(s) of {w["label"]} on one host core (FP64 C oracle)'),
+                e2e=dict(value=r['mlups'], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    assert ws == args.gpus, f'--gpus {args.gpus} but WORLD_SIZE {ws}'
+    torch.cuda.set_device(local)
+    device = torch.device('cuda', local)
+    dist = init_dist(ws, 'nccl')
+    from paper_1704_04551_gb300 import binding, build
+    build.build()
+    w = make_workload(args.workload)
+    storage = args.storage or w['storage']
+    lat = w['lattice']
+    N = lat['nx'] * lat['ny'] * lat['nz']
+    Nf = fluid_cells(lat)
+    M = int(w['X'].shape[1])
+
+    sim = binding.Simulation.from_workload(w, storage=storage, device=local)
+    stream = torch.cuda.ExternalStream(sim.stream, device=device)
+    sim.step(args.warmup)
+
+    # ---- timed region: K steps, inputs resident in HBM -----------------------
+    sim.set_timing(args.steps)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    time.sleep(0.3)
+    start.record(stream)
+    sim.step_async(args.steps)
+    end.record(stream)
+    sim.synchronize()
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(dist, device)
+    ms = start.elapsed_time(end)
+    ms_max = reduce_max(dist, ms, device)
+    stages = sim.timing()
+    sim.set_timing(0)
+    # the same steps through the CUDA-graph path (production launch mode)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    g0.record(stream)
+    sim.step_async(args.steps)
+    g1.record(stream)
+    sim.synchronize()
+    graph_ms = g0.elapsed_time(g1)
+    diag = sim.diagnostics()
+    value = aggregate(N * args.steps, ms_max / 1e3, ws) / 1e6
+
+    # ---- roofline of the collide-stream kernel -------------------------------
+    sp = bytes_per_pop(storage)
+    n_touch = touched_cells(lat, w['X'])
+    alg_bytes = Nf * 38 * sp + n_touch * 24
+    collide_s = stages['collide_ms'] / 1e3 / max(1, stages['steps'])
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / collide_s / 1e9
+    step_alg = alg_bytes + M * 72
+    roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
+                traffic=collide_traffic(storage), kernel='k_collide (fused collide-stream-force)',
+                peak_source=f'{peak_kind} hbm_gbs (burst copy)',
+                alg_bytes_per_launch=alg_bytes, step_alg_bytes=step_alg,
+                step_frac=(step_alg / (ms_max / 1e3 / args.steps) / 1e9) / peak)
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    rho0 = np.ones(N)
+    u0 = np.zeros((3, N))
+    X0 = np.ascontiguousarray(w['X'])
+    rho_out = np.empty(N)
+    u_out = np.empty((3, N))
+    Xo, Uo, Fo = np.empty((3, M)), np.empty((3, M)), np.empty((3, M))
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    binding.ibm_lbm_set_lattice(sim.h, rho0, u0)
+    sim.set_markers(w.get('mesh'), w['bodies'], X0)
+    binding.ibm_lbm_step(sim.h, args.steps)
+    binding.ibm_lbm_get_fields(sim.h, rho_out, u_out)
+    binding.ibm_lbm_get_markers(sim.h, Xo, Uo, Fo)
+    e2e_s = reduce_max(dist, time.perf_counter() - t0, device)
+    h2d = rho0.nbytes + u0.nbytes + X0.nbytes
+    d2h = rho_out.nbytes + u_out.nbytes + Xo.nbytes + Uo.nbytes + Fo.nbytes
+    e2e = dict(value=aggregate(N * args.steps, e2e_s, ws) / 1e6, unit=UNIT,
+               h2d_bytes_per_step=h2d / args.steps, d2h_bytes_per_step=d2h / args.steps,
+               note='one job: upload lattice state + markers, K steps, download fields + markers; bytes/step = job bytes / K')
+
+    # ---- CPU baseline (rank 0, N = 1 only) -----------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        r = time_oracle(w, 1)
+        cpu = dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
+                   sample=f'1 full coupled step of {w["label"]} (FP64 C oracle, single thread, setup excluded)',
+                   seconds=r['seconds'])
+
+    if rank == 0:
+        tot = sum(stages[k] for k in ('forces_ms', 'spread_ms', 'collide_ms', 'interp_ms'))
+        split = {k: stages[k] / max(1, stages['steps']) for k in ('forces_ms', 'spread_ms', 'collide_ms', 'interp_ms')}
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+            ms_per_step=ms_max / args.steps, higher_is_better=True, scaling='weak', vs_baseline=None,
+            dtype='f32' if storage == 'f32' else f'f32 ({storage}-deviation storage)', data='synthetic',
+            config=dict(workload=w['label'], lattice=[lat['nx'], lat['ny'], lat['nz']], fluid_cells=Nf,
+                        touched_cells=n_touch, markers=M, bodies=len(w['bodies']), tau=lat['tau'],
+                        body_force=lat['body_force'][0], storage=storage, seed=w['seed'],
+                        mflups_fluid=Nf * args.steps * ws / (ms_max / 1e3) / 1e6,
+                        graph_path_ms_per_step=graph_ms / args.steps,
+                        stage_ms_per_step=split,
+                        coupling_share=(split['spread_ms'] + split['interp_ms']) / max(1e-12, sum(split.values())),
+                        l2='inputs larger than L2 (populations %.2f GB)' % (19 * N * sp / 1e9),
+                        parallelism=f'replicas x{ws}' if ws > 1 else 'single GPU'),
+            roofline=roof, cpu_baseline=cpu, e2e=e2e,
+            clocks=dict(sm_mhz=clk['sm_mhz'], sm_max_mhz=clk['sm_max_mhz'], reasons=clk['reasons'],
+                        samples=clk['samples']),
+            gpu_launches=4 * args.steps + 1,
+            diagnostics=dict(mass=diag['mass'], fluid_cells=diag['fluid_cells'], umax=diag['umax']),
+            timed_stage_total_ms=tot)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=1000)
+    ap.add_argument('--warmup', type=int, default=20)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--workload', default='tube256', choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube64', 'shear32'])
+    ap.add_argument('--storage', default=None, choices=[None, 'f32', 'f16', 'bf16'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--ref-max-steps', type=int, default=2)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit('--warmup must be >= 3')
+    if args.impl == 'reference':
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == '__main__':
+    sys.exit(main())

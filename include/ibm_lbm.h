@@ -1,0 +1,215 @@
+/*
+ * ibm_lbm.h — C ABI of the GB300 (sm_103a) coupled immersed-boundary /
+ * lattice-Boltzmann time step of Tan, Sinno & Diamond, "A parallel fluid
+ * solid coupling model using LAMMPS and Palabos based on the immersed
+ * boundary method" (arXiv:1704.04551).
+ *
+ * One time step, in this order (the paper does not print the order; this
+ * library and its test oracle use the same reading):
+ *   1. marker forces at X^n — membrane forces -dU/dX of Eq. membrane-potential
+ *      (Eqs. inPlanePotential, bendingEnergy, areaEnergy, volumeEnergy,
+ *      Sec. 2.2), or a rigid body's penalty tether with a Newton-Euler update
+ *      of the body (Sec. 2.3);
+ *   2. spreading of marker forces to the lattice, Eq. ibmForceSpread, with the
+ *      4-point cosine delta of Eq. deltaPhiSimple;
+ *   3. D3Q19 BGK collision with Guo forcing and streaming, Eqs. lbm,
+ *      BGKequilibrium, rho_u and the Guo term (Sec. 2.1), half-way
+ *      bounce-back at walls;
+ *   4. interpolation of the collision-time lattice velocity to the markers,
+ *      Eq. ibmVelocityInterpret, and advection X^{n+1} = X^n + U.
+ * These are the two coupling routines of the paper's List 1
+ * (interpolateVelocity3D / spreadForce3D) plus the fluid and solid steps
+ * they connect.
+ *
+ * Conventions (every entry point):
+ *   - Lattice units: dx = dt = 1, fluid density ~1, c_s^2 = 1/3.
+ *   - Cell index idx = x + nx*(y + ny*z); cell (x,y,z) sits at position
+ *     (x,y,z). Scalar fields are [N], vector fields [3][N] (component
+ *     major), populations [19][N], marker arrays [3][M]; all host arrays are
+ *     dense, C order, owned by the caller, and only read or written during
+ *     the call (the library keeps no host pointer).
+ *   - D3Q19 order: 0 (0,0,0); 1,2 (+-1,0,0); 3,4 (0,+-1,0); 5,6 (0,0,+-1);
+ *     7,8 +-(1,1,0); 9,10 +-(1,-1,0); 11,12 +-(1,0,1); 13,14 +-(1,0,-1);
+ *     15,16 +-(0,1,1); 17,18 +-(0,1,-1). Weights 1/3, 1/18, 1/36.
+ *   - Every call returns an ibm_lbm_status (0 = OK, negative = error) and
+ *     never aborts; ibm_lbm_last_error() gives the message of the last
+ *     failure on that handle. A handle may be used from one host thread at
+ *     a time.
+ *   - Device memory is owned by the handle and allocated at create /
+ *     set_markers time through the caller's allocator (or cudaMalloc when
+ *     none is given). Stepping allocates nothing.
+ */
+#ifndef IBM_LBM_H
+#define IBM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IBM_LBM_OK = 0,
+  IBM_LBM_E_ARG = -1,      /* invalid argument (sizes, ranges, mesh topology) */
+  IBM_LBM_E_NOMEM = -2,    /* the allocator returned NULL */
+  IBM_LBM_E_CUDA = -3,     /* a CUDA runtime call failed */
+  IBM_LBM_E_UNSTABLE = -4, /* non-finite or |u| > 0.4 found by the end-of-call check */
+  IBM_LBM_E_TIMEOUT = -5,  /* a bounded wait gave up */
+  IBM_LBM_E_STATE = -6     /* call not valid in the handle's current state */
+} ibm_lbm_status;
+
+enum { IBM_LBM_STORE_F32 = 0, IBM_LBM_STORE_F16_DEV = 1, IBM_LBM_STORE_BF16_DEV = 2 };
+enum { IBM_LBM_GEOM_PERIODIC = 0, IBM_LBM_GEOM_YWALLS = 1, IBM_LBM_GEOM_TUBE = 2 };
+enum { IBM_LBM_BODY_MEMBRANE = 0, IBM_LBM_BODY_RIGID = 1 };
+enum { IBM_LBM_STAGE_FORCES = 0, IBM_LBM_STAGE_SPREAD = 1, IBM_LBM_STAGE_COLLIDE = 2,
+       IBM_LBM_STAGE_INTERP = 3 };
+
+/* Device-memory provider. alloc returns a device pointer aligned to at
+ * least 256 bytes, or NULL; release frees it. Called only from create,
+ * set_markers and destroy, on the calling thread. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*release)(void* ptr, void* ctx);
+  void* ctx;
+} ibm_lbm_allocator;
+
+/* Lattice description (Sec. 2.1). */
+typedef struct {
+  int32_t nx, ny, nz;   /* cells; each >= 4, N = nx*ny*nz < 2^31 */
+  int32_t geometry;     /* IBM_LBM_GEOM_*: periodic box; walls at y = -1/2 and
+                           y = ny - 1/2 (periodic x, z); tube along x whose
+                           solid cells lie farther than tube_radius from the
+                           axis y = (ny-1)/2, z = (nz-1)/2 (periodic x) */
+  double tau;           /* BGK relaxation time > 1/2; nu = (tau - 1/2)/3 (Eq. viscosity) */
+  double wall_u[2];     /* x velocity of the y = -1/2 and y = ny - 1/2 walls */
+  double tube_radius;
+  double body_force[3]; /* uniform force density g0 added to the spread one */
+  int32_t storage;      /* IBM_LBM_STORE_*: populations stored as FP32 deviations
+                           f_i - w_i, or as FP16 / BF16 scaled deviations
+                           K_i (f_i - w_i), K = 4, 16, 32 for rest, axis, diagonal;
+                           all arithmetic is FP32 */
+  int32_t device;       /* CUDA device ordinal */
+} ibm_lbm_config;
+
+/* One immersed body: a contiguous range of markers. Membranes use the
+ * template mesh of ibm_lbm_set_markers (count == its vertex count). Rigid
+ * bodies tether each marker to a body-fixed point (penalty reading of the
+ * rigid coupling of Sec. 2.3, Eq. FSIRigid): force on the fluid
+ * F_k = -kappa (X_k - X_k^ref), reaction on the body, explicit Newton-Euler
+ * update of the pose. */
+typedef struct {
+  int32_t kind;                 /* IBM_LBM_BODY_* */
+  int32_t pad;
+  int64_t first, count;         /* marker range */
+  double kBT_p, k_b, k_l, k_g, k_v;  /* membrane: kBT/p, bending, local/global
+                                        area, volume moduli (Eqs. inPlanePotential,
+                                        bendingEnergy, areaEnergy, volumeEnergy) */
+  double kappa;                 /* rigid: tether stiffness */
+  double mass, inertia[3];      /* rigid: mass and principal moments (body frame) */
+  double center[3], quat[4];    /* rigid: centre, unit quaternion (w,x,y,z) body->world */
+  double vel[3], omega[3];      /* rigid: velocity, angular velocity (world frame) */
+} ibm_lbm_body;
+
+/* Membrane template (Sec. 2.2): closed, consistently outward-oriented
+ * triangle mesh. Rest edge lengths, rest dihedral angles, rest triangle
+ * areas, rest total area and volume are taken from rest_X. */
+typedef struct {
+  int32_t n_vertices;      /* <= 4096 */
+  int32_t n_triangles;
+  const int32_t* tris;     /* host [n_triangles][3], counter-clockwise seen from outside */
+  const double* rest_X;    /* host [3][n_vertices] */
+} ibm_lbm_mesh;
+
+typedef struct ibm_lbm ibm_lbm_t;
+
+/* Create a lattice at rest (rho = 1, u = 0 at equilibrium, Sec. 2.1).
+ * alloc may be NULL (cudaMalloc/cudaFree). stream is a cudaStream_t or NULL
+ * (the handle then creates its own non-blocking stream); all work of the
+ * handle is ordered on that stream. Errors: E_ARG, E_NOMEM, E_CUDA. */
+int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
+                   ibm_lbm_t** out);
+
+/* Synchronise the stream and release all device memory. NULL is a no-op. */
+int ibm_lbm_destroy(ibm_lbm_t* h);
+
+/* Initialise every fluid cell at equilibrium f = f^eq(rho, u) (Sec. 2.1,
+ * Eq. BGKequilibrium). rho: host [N] or NULL (= 1); u: host [3][N] or NULL
+ * (= 0). Resets the step counter and clears spread forces. */
+int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u);
+
+/* Raw populations f_i (not deviations), host [19][N] FP64, in the natural
+ * (pre-collision) layout of the D3Q19 order above. set resets the step
+ * parity; values are rounded to the storage format. */
+int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f);
+int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
+
+/* Markers, bodies and (optional) membrane template. mesh may be NULL when
+ * no body is a membrane. X: host [3][n_markers]. Markers outside every
+ * body are passive tracers (zero force). Errors: E_ARG (overlapping or
+ * out-of-range bodies, membrane count != n_vertices, non-manifold mesh,
+ * n_vertices > 4096), E_NOMEM. */
+int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
+                        const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
+
+/* Advance n_steps coupled steps (order above) and wait for them; the last
+ * step also writes the moments of every fluid cell and a FP64 conservation
+ * check runs (E_UNSTABLE on a non-finite value or |u| > 0.4). */
+int ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps);
+/* Same work, enqueued without waiting; ibm_lbm_synchronize waits and
+ * returns the status of everything enqueued since the last wait. */
+int ibm_lbm_step_async(ibm_lbm_t* h, int64_t n_steps);
+int ibm_lbm_synchronize(ibm_lbm_t* h);
+
+/* Moments of the last collision (Eq. rho_u, including half the force
+ * density): rho host [N], u host [3][N]; either may be NULL. Solid cells
+ * report rho = 0, u = 0. Before any step: the state given to set_lattice. */
+int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u);
+
+/* Markers: X host [3][M] FP64; U (last interpolated velocity, Eq.
+ * ibmVelocityInterpret) and F (last marker force) host [3][M] FP64; any
+ * may be NULL. */
+int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F);
+/* Body records with the current rigid-body state (pose, velocities). */
+int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies);
+
+/* Diagnostics of the last ibm_lbm_step (FP64 sums over fluid cells of the
+ * last collision's moments): out[0] = sum rho, out[1..3] = sum rho u,
+ * out[4] = max |u|, out[5] = steps taken since set_lattice,
+ * out[6] = fluid cell count, out[7] = 0. */
+int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]);
+
+/* Stage-by-stage execution for verification: runs one stage of the step
+ * (IBM_LBM_STAGE_*) on the handle's stream and waits. COLLIDE writes the
+ * moments of every fluid cell; INTERP completes the step. */
+int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage);
+/* Overwrite the marker forces (host [3][M]) read by the next SPREAD stage. */
+int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F);
+/* The spread force density waiting for the next COLLIDE (excluding the
+ * uniform body force), host [3][N]. */
+int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
+
+/* Per-stage timing with CUDA events on the handle's stream (measurement
+ * support; no counterpart in the paper beyond its gprof split of the coupling
+ * routines, Table tab:timeCoupling). ibm_lbm_set_timing(h, n) with n > 0
+ * pre-creates events for n steps and makes the following steps launch their
+ * kernels directly (not through graphs) with an event between stages;
+ * n = 0 turns timing off. ibm_lbm_get_timing waits for the stream and
+ * returns, summed over the timed steps, the milliseconds of out[0] marker
+ * forces, out[1] spreading, out[2] collide-stream, out[3] interpolation,
+ * and out[4] = number of timed steps; then resets the sums. */
+int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps);
+int ibm_lbm_get_timing(ibm_lbm_t* h, double out[5]);
+
+/* The cudaStream_t the handle works on. */
+void* ibm_lbm_stream(ibm_lbm_t* h);
+/* Bytes of device memory the handle holds. */
+size_t ibm_lbm_device_bytes(const ibm_lbm_t* h);
+/* Message of the last failed call on h (static text for h == NULL). */
+const char* ibm_lbm_last_error(const ibm_lbm_t* h);
+const char* ibm_lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBM_LBM_H */

@@ -1,0 +1,785 @@
+// C ABI of the coupled IBM-LBM step (include/ibm_lbm.h): handle lifetime,
+// device memory, host<->device conversion, validation, and the step loop
+// (captured into CUDA graphs: one graph per 16 steps, plus single steps).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ibm_lbm.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace ibm;
+
+namespace {
+
+constexpr int CHUNK = 16;          // steps per captured chunk graph (even)
+constexpr int MAX_MESH_VERTICES = 4096;
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct ibm_lbm {
+  ibm_lbm_config cfg{};
+  ibm_lbm_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  LatticeDev L{};
+  std::vector<Alloc> lattice_mem, marker_mem;
+  size_t bytes = 0;
+  // markers
+  MarkersDev m{};
+  int n_bodies = 0;
+  BodyDev* d_bodies = nullptr;
+  std::vector<ibm_lbm_body> h_bodies;
+  MeshDev mesh{};
+  bool need_zero_F = false;
+  // state
+  long long steps = 0;
+  bool odd_next = false;          // the array is in the post-even-step layout
+  double* d_diag = nullptr;       // [8]
+  unsigned* d_umax = nullptr;
+  double* h_diag = nullptr;       // pinned [8]
+  unsigned* h_umax = nullptr;     // pinned
+  int* h_status = nullptr;        // pinned
+  bool diag_pending = false;
+  // per-stage timing (events between stages, direct launches)
+  std::vector<cudaEvent_t> events;  // 5 per timed step
+  size_t timed_steps = 0;
+  bool timing = false;
+  // graphs
+  cudaGraphExec_t g_chunk = nullptr;
+  cudaGraphExec_t g_single[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  std::string err;
+};
+
+namespace {
+
+int fail(ibm_lbm_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((h), IBM_LBM_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));   \
+  } while (0)
+
+void* dalloc(ibm_lbm_t* h, std::vector<Alloc>& pool, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (h->has_alloc) {
+    p = h->alloc.alloc(bytes, h->alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    pool.push_back({p, bytes});
+    h->bytes += bytes;
+  }
+  return p;
+}
+
+void release_pool(ibm_lbm_t* h, std::vector<Alloc>& pool) {
+  for (auto& a : pool) {
+    if (h->has_alloc) h->alloc.release(a.p, h->alloc.ctx);
+    else cudaFree(a.p);
+    h->bytes -= a.bytes;
+  }
+  pool.clear();
+}
+
+void drop_graphs(ibm_lbm_t* h) {
+  if (h->g_chunk) cudaGraphExecDestroy(h->g_chunk);
+  h->g_chunk = nullptr;
+  for (auto& row : h->g_single)
+    for (auto& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int tiles(const LatticeDev& L) { return L.ntx * L.nty * L.ntz; }
+
+// One coupled step on the handle's stream (also used under capture).
+void enqueue_step(ibm_lbm_t* h, bool odd, bool dense) {
+  cudaStream_t st = h->stream;
+  cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st);
+  if (h->m.M > 0) {
+    if (h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
+    launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
+    launch_spread(h->L, h->m, st);
+  }
+  launch_collide(h->L, h->cfg.storage, odd, dense, st);
+  if (h->m.M > 0) launch_interpolate(h->L, h->m, st);
+}
+
+// One step with an event before each stage and after the last.
+void enqueue_timed_step(ibm_lbm_t* h, bool odd, bool dense) {
+  cudaStream_t st = h->stream;
+  const size_t base = 5 * h->timed_steps;
+  const bool rec = base + 5 <= h->events.size();
+  auto mark = [&](int k) {
+    if (rec) cudaEventRecord(h->events[base + k], st);
+  };
+  cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st);
+  if (h->m.M > 0 && h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
+  mark(0);
+  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
+  mark(1);
+  if (h->m.M > 0) launch_spread(h->L, h->m, st);
+  mark(2);
+  launch_collide(h->L, h->cfg.storage, odd, dense, st);
+  mark(3);
+  if (h->m.M > 0) launch_interpolate(h->L, h->m, st);
+  mark(4);
+  if (rec) h->timed_steps++;
+}
+
+int capture(ibm_lbm_t* h, cudaGraphExec_t* out, int n, bool odd0, bool dense_last) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  bool odd = odd0;
+  for (int s = 0; s < n; ++s) {
+    enqueue_step(h, odd, dense_last && s == n - 1);
+    odd = !odd;
+  }
+  CUDA_TRY(h, cudaStreamEndCapture(h->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, IBM_LBM_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return IBM_LBM_OK;
+}
+
+int enqueue_diagnostics(ibm_lbm_t* h) {
+  cudaStream_t st = h->stream;
+  CUDA_TRY(h, cudaMemsetAsync(h->d_diag, 0, 8 * sizeof(double), st));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_umax, 0, sizeof(unsigned), st));
+  launch_diagnostics(h->L, h->d_diag, h->d_umax, st);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_diag, h->d_diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_umax, h->d_umax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_status, h->L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->diag_pending = true;
+  return IBM_LBM_OK;
+}
+
+int finish_diagnostics(ibm_lbm_t* h) {
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (!h->diag_pending) return IBM_LBM_OK;
+  h->diag_pending = false;
+  float umax2;
+  std::memcpy(&umax2, h->h_umax, sizeof(float));
+  if (*h->h_status != 0 || !std::isfinite(umax2) || umax2 > 0.16f) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "unstable: non-finite moments or |u| > 0.4 (max |u|^2 = %g) after %lld steps",
+                  (double)umax2, h->steps);
+    return fail(h, IBM_LBM_E_UNSTABLE, buf);
+  }
+  return IBM_LBM_OK;
+}
+
+int enqueue_steps(ibm_lbm_t* h, int64_t n) {
+  if (n < 0) return fail(h, IBM_LBM_E_ARG, "n_steps < 0");
+  if (n == 0) return IBM_LBM_OK;
+  int64_t left = n;
+  if (h->timing) {
+    for (; left > 0; --left) {
+      enqueue_timed_step(h, h->odd_next, left == 1);
+      h->steps += 1;
+      h->odd_next = !h->odd_next;
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    return enqueue_diagnostics(h);
+  }
+  while (left > 0) {
+    if (!h->odd_next && left > CHUNK) {
+      if (!h->g_chunk) {
+        int rc = capture(h, &h->g_chunk, CHUNK, false, false);
+        if (rc) return rc;
+      }
+      CUDA_TRY(h, cudaGraphLaunch(h->g_chunk, h->stream));
+      left -= CHUNK;
+      h->steps += CHUNK;
+    } else {
+      const int odd = h->odd_next ? 1 : 0, dense = (left == 1) ? 1 : 0;
+      if (!h->g_single[odd][dense]) {
+        int rc = capture(h, &h->g_single[odd][dense], 1, odd, dense);
+        if (rc) return rc;
+      }
+      CUDA_TRY(h, cudaGraphLaunch(h->g_single[odd][dense], h->stream));
+      left -= 1;
+      h->steps += 1;
+      h->odd_next = !h->odd_next;
+    }
+  }
+  return enqueue_diagnostics(h);
+}
+
+// ---- membrane template: edges and rest state (FP64) --------------------------
+struct HostMesh {
+  std::vector<int4> edges;
+  std::vector<float2> edge_rest;
+  std::vector<int4> tris;
+  std::vector<float> area0;
+  double A0 = 0, V0 = 0;
+};
+
+struct V3 {
+  double x, y, z;
+};
+V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 crs(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double dt3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
+  const int nv = mesh->n_vertices, nt = mesh->n_triangles;
+  if (nv < 4 || nv > MAX_MESH_VERTICES || nt < 4 || !mesh->tris || !mesh->rest_X) {
+    why = "mesh: need 4 <= n_vertices <= 4096, n_triangles >= 4 and both arrays";
+    return false;
+  }
+  auto P = [&](int v) { return V3{mesh->rest_X[v], mesh->rest_X[nv + v], mesh->rest_X[2 * nv + v]}; };
+  std::unordered_map<uint64_t, int> emap;
+  out.edges.clear();
+  out.tris.resize(nt);
+  for (int t = 0; t < nt; ++t) {
+    int v[3] = {mesh->tris[3 * t], mesh->tris[3 * t + 1], mesh->tris[3 * t + 2]};
+    for (int s = 0; s < 3; ++s)
+      if (v[s] < 0 || v[s] >= nv) {
+        why = "mesh: triangle vertex index out of range";
+        return false;
+      }
+    out.tris[t] = make_int4(v[0], v[1], v[2], 0);
+    for (int s = 0; s < 3; ++s) {
+      const int a = v[s], b = v[(s + 1) % 3], c = v[(s + 2) % 3];
+      const uint64_t key = ((uint64_t)std::min(a, b) << 32) | (uint32_t)std::max(a, b);
+      auto it = emap.find(key);
+      if (it == emap.end()) {
+        emap.emplace(key, (int)out.edges.size());
+        out.edges.push_back(make_int4(a, b, c, -1));
+      } else {
+        int4& e = out.edges[it->second];
+        if (e.w >= 0 || e.x != b || e.y != a) {
+          why = "mesh: not a closed, consistently oriented 2-manifold";
+          return false;
+        }
+        e.w = c;
+      }
+    }
+  }
+  for (auto& e : out.edges)
+    if (e.w < 0) {
+      why = "mesh: open boundary edge";
+      return false;
+    }
+  out.edge_rest.resize(out.edges.size());
+  for (size_t i = 0; i < out.edges.size(); ++i) {
+    const int4 e = out.edges[i];
+    V3 a = P(e.x), b = P(e.y), c = P(e.z), d = P(e.w);
+    V3 ev = sub(b, a);
+    V3 n1 = crs(ev, sub(c, a)), n2 = crs(sub(a, b), sub(d, b));
+    const double L = std::sqrt(dt3(ev, ev));
+    const double th = std::atan2(dt3(crs(n1, n2), ev) / L, dt3(n1, n2));
+    out.edge_rest[i] = make_float2((float)L, (float)th);
+  }
+  out.area0.resize(nt);
+  out.A0 = out.V0 = 0;
+  for (int t = 0; t < nt; ++t) {
+    V3 p0 = P(out.tris[t].x), p1 = P(out.tris[t].y), p2 = P(out.tris[t].z);
+    V3 N = crs(sub(p1, p0), sub(p2, p0));
+    const double A = 0.5 * std::sqrt(dt3(N, N));
+    out.area0[t] = (float)A;
+    out.A0 += A;
+    out.V0 += dt3(p0, crs(p1, p2)) / 6.0;
+  }
+  if (!(out.V0 > 0)) {
+    why = "mesh: non-positive rest volume (triangles must be counter-clockwise seen from outside)";
+    return false;
+  }
+  return true;
+}
+
+template <typename T>
+int upload(ibm_lbm_t* h, std::vector<Alloc>& pool, T** dst, const T* src, size_t count) {
+  *dst = static_cast<T*>(dalloc(h, pool, sizeof(T) * count));
+  if (!*dst) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  if (count) CUDA_TRY(h, cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+  return IBM_LBM_OK;
+}
+
+void quat_matrix(const double q[4], double R[3][3]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+  R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+  R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+bool fluid_yz(const LatticeDev& L, int y, int z) {
+  if (L.geometry == GEOM_YWALLS) return y >= 0 && y < L.ny;
+  if (L.geometry == GEOM_TUBE) {
+    if (y < 0 || y >= L.ny || z < 0 || z >= L.nz) return false;
+    const float dy = (float)y - L.yc, dz = (float)z - L.zc;
+    return !(dy * dy + dz * dz > L.R2);
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ibm_lbm_version(void) { return "ibm_lbm 0.1 (sm_103a)"; }
+
+const char* ibm_lbm_last_error(const ibm_lbm_t* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+void* ibm_lbm_stream(ibm_lbm_t* h) { return h ? (void*)h->stream : nullptr; }
+
+size_t ibm_lbm_device_bytes(const ibm_lbm_t* h) { return h ? h->bytes : 0; }
+
+int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, void* stream, ibm_lbm_t** out) {
+  if (!cfg || !out) return IBM_LBM_E_ARG;
+  *out = nullptr;
+  const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  if (cfg->nx < 4 || cfg->ny < 4 || cfg->nz < 4 || N >= (1LL << 31)) return IBM_LBM_E_ARG;
+  if (!(cfg->tau > 0.5) || cfg->geometry < 0 || cfg->geometry > 2 || cfg->storage < 0 || cfg->storage > 2)
+    return IBM_LBM_E_ARG;
+  if (cfg->geometry == 2 && !(cfg->tube_radius > 0)) return IBM_LBM_E_ARG;
+  if (alloc && (!alloc->alloc || !alloc->release)) return IBM_LBM_E_ARG;
+  ibm_lbm_t* h = new ibm_lbm_t();
+  h->cfg = *cfg;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  auto bail = [&](int code) {
+    ibm_lbm_destroy(h);
+    return code;
+  };
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(IBM_LBM_E_CUDA);
+  }
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(IBM_LBM_E_CUDA);
+    h->own_stream = true;
+  }
+  LatticeDev& L = h->L;
+  L.nx = cfg->nx; L.ny = cfg->ny; L.nz = cfg->nz; L.N = (int)N;
+  L.geometry = cfg->geometry;
+  L.omega = (float)(1.0 / cfg->tau);
+  L.guo_pre = (float)(1.0 - 0.5 / cfg->tau);
+  L.wall_u0 = (float)cfg->wall_u[0]; L.wall_u1 = (float)cfg->wall_u[1];
+  L.yc = 0.5f * (float)(cfg->ny - 1); L.zc = 0.5f * (float)(cfg->nz - 1);
+  L.R2 = (float)(cfg->tube_radius * cfg->tube_radius);
+  L.g0x = (float)cfg->body_force[0]; L.g0y = (float)cfg->body_force[1]; L.g0z = (float)cfg->body_force[2];
+  L.ntx = (cfg->nx + 31) >> TILE_X_SHIFT;
+  L.nty = (cfg->ny + 3) >> TILE_Y_SHIFT;
+  L.ntz = (cfg->nz + 3) >> TILE_Z_SHIFT;
+  const size_t sp = cfg->storage == STORE_F32 ? 4 : 2;
+  L.pop = dalloc(h, h->lattice_mem, (size_t)Q * N * sp);
+  L.uw = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
+  L.g = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
+  L.flags = (uint8_t*)dalloc(h, h->lattice_mem, (size_t)tiles(L));
+  L.status = (int*)dalloc(h, h->lattice_mem, 256);
+  h->d_diag = (double*)dalloc(h, h->lattice_mem, 8 * sizeof(double));
+  h->d_umax = (unsigned*)dalloc(h, h->lattice_mem, 256);
+  if (!L.pop || !L.uw || !L.g || !L.flags || !L.status || !h->d_diag || !h->d_umax) {
+    h->err = "device allocation failed";
+    return bail(IBM_LBM_E_NOMEM);
+  }
+  if (cudaMallocHost((void**)&h->h_diag, 8 * sizeof(double) + 2 * sizeof(unsigned) + sizeof(int)) != cudaSuccess)
+    return bail(IBM_LBM_E_NOMEM);
+  h->h_umax = reinterpret_cast<unsigned*>(h->h_diag + 8);
+  h->h_status = reinterpret_cast<int*>(h->h_umax + 2);
+  if (cudaMemsetAsync(L.status, 0, sizeof(int), h->stream) != cudaSuccess) return bail(IBM_LBM_E_CUDA);
+  int rc = ibm_lbm_set_lattice(h, nullptr, nullptr);
+  if (rc) return bail(rc);
+  *out = h;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_destroy(ibm_lbm_t* h) {
+  if (!h) return IBM_LBM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto e : h->events) cudaEventDestroy(e);
+  h->events.clear();
+  drop_graphs(h);
+  release_pool(h, h->marker_mem);
+  release_pool(h, h->lattice_mem);
+  if (h->h_diag) cudaFreeHost(h->h_diag);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
+  if (!h) return IBM_LBM_E_ARG;
+  LatticeDev& L = h->L;
+  const size_t N = (size_t)L.N;
+  std::vector<float4> m(N);
+  for (size_t i = 0; i < N; ++i) {
+    const double r = rho ? rho[i] : 1.0;
+    m[i] = make_float4(u ? (float)u[i] : 0.f, u ? (float)u[N + i] : 0.f, u ? (float)u[2 * N + i] : 0.f,
+                       (float)(r - 1.0));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(L.uw, m.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, h->stream));
+  launch_init_equilibrium(L, h->cfg.storage, h->stream);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemsetAsync(L.g, 0, sizeof(float4) * N, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(L.status, 0, sizeof(int), h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->steps = 0;
+  h->odd_next = false;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
+  if (!h || !f) return fail(h, IBM_LBM_E_ARG, "null argument");
+  std::vector<Alloc> tmp;
+  const size_t bytes = sizeof(double) * Q * (size_t)h->L.N;
+  double* d = (double*)dalloc(h, tmp, bytes);
+  if (!d) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  int rc = IBM_LBM_OK;
+  if (cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) rc = IBM_LBM_E_CUDA;
+  if (!rc) {
+    launch_import(h->L, h->cfg.storage, d, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IBM_LBM_E_CUDA;
+  }
+  release_pool(h, tmp);
+  if (rc) return fail(h, rc, "set_populations: CUDA error");
+  h->odd_next = false;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
+  if (!h || !f) return fail(h, IBM_LBM_E_ARG, "null argument");
+  std::vector<Alloc> tmp;
+  const size_t bytes = sizeof(double) * Q * (size_t)h->L.N;
+  double* d = (double*)dalloc(h, tmp, bytes);
+  if (!d) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  launch_export(h->L, h->cfg.storage, h->odd_next, d, h->stream);
+  int rc = IBM_LBM_OK;
+  if (cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  release_pool(h, tmp);
+  if (rc) return fail(h, rc, "get_populations: CUDA error");
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
+                        int64_t n_markers, const double* X) {
+  if (!h) return IBM_LBM_E_ARG;
+  if (n_bodies < 0 || n_markers < 0 || n_markers >= (1LL << 31) || (n_markers > 0 && !X) ||
+      (n_bodies > 0 && !bodies))
+    return fail(h, IBM_LBM_E_ARG, "set_markers: bad counts or null arrays");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  release_pool(h, h->marker_mem);
+  h->m = MarkersDev{};
+  h->n_bodies = 0;
+  h->d_bodies = nullptr;
+  h->h_bodies.clear();
+  h->mesh = MeshDev{};
+  const int M = (int)n_markers;
+  // validate bodies
+  std::vector<std::pair<int64_t, int64_t>> ranges;
+  bool any_membrane = false, any_rigid = false;
+  int64_t covered = 0;
+  for (int b = 0; b < n_bodies; ++b) {
+    const ibm_lbm_body& B = bodies[b];
+    if (B.first < 0 || B.count <= 0 || B.first + B.count > n_markers)
+      return fail(h, IBM_LBM_E_ARG, "set_markers: body marker range out of bounds");
+    if (B.kind == IBM_LBM_BODY_MEMBRANE) {
+      any_membrane = true;
+      if (!mesh) return fail(h, IBM_LBM_E_ARG, "set_markers: membrane body without a mesh");
+      if (B.count != mesh->n_vertices)
+        return fail(h, IBM_LBM_E_ARG, "set_markers: membrane marker count != mesh vertex count");
+    } else if (B.kind == IBM_LBM_BODY_RIGID) {
+      any_rigid = true;
+      if (!(B.mass > 0) || !(B.inertia[0] > 0) || !(B.inertia[1] > 0) || !(B.inertia[2] > 0) || !(B.kappa >= 0))
+        return fail(h, IBM_LBM_E_ARG, "set_markers: rigid body needs mass, inertia > 0 and kappa >= 0");
+    } else {
+      return fail(h, IBM_LBM_E_ARG, "set_markers: unknown body kind");
+    }
+    ranges.push_back({B.first, B.first + B.count});
+    covered += B.count;
+  }
+  std::sort(ranges.begin(), ranges.end());
+  for (size_t i = 1; i < ranges.size(); ++i)
+    if (ranges[i].first < ranges[i - 1].second) return fail(h, IBM_LBM_E_ARG, "set_markers: bodies overlap");
+  HostMesh hm;
+  if (any_membrane) {
+    std::string why;
+    if (!build_mesh(mesh, hm, why)) return fail(h, IBM_LBM_E_ARG, why);
+    const size_t smem = forces_smem_bytes(mesh->n_vertices);
+    if (smem > 48 * 1024) CUDA_TRY(h, forces_configure(smem));
+  }
+  int rc;
+  // marker arrays
+  h->m.M = M;
+  if ((rc = upload<double>(h, h->marker_mem, &h->m.X, X, 3 * (size_t)M))) return rc;
+  h->m.U = (float4*)dalloc(h, h->marker_mem, sizeof(float4) * (size_t)M);
+  h->m.F = (float4*)dalloc(h, h->marker_mem, sizeof(float4) * (size_t)M);
+  if (!h->m.U || !h->m.F) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  CUDA_TRY(h, cudaMemset(h->m.U, 0, sizeof(float4) * (size_t)std::max(M, 1)));
+  CUDA_TRY(h, cudaMemset(h->m.F, 0, sizeof(float4) * (size_t)std::max(M, 1)));
+  // rigid body-frame offsets r_k = R^T (X_k - C)
+  if (any_rigid) {
+    std::vector<double> ref(3 * (size_t)M, 0.0);
+    for (int b = 0; b < n_bodies; ++b) {
+      const ibm_lbm_body& B = bodies[b];
+      if (B.kind != IBM_LBM_BODY_RIGID) continue;
+      double R[3][3];
+      quat_matrix(B.quat, R);
+      for (int64_t k = B.first; k < B.first + B.count; ++k) {
+        const double d[3] = {X[k] - B.center[0], X[M + k] - B.center[1], X[2 * (size_t)M + k] - B.center[2]};
+        for (int a = 0; a < 3; ++a) ref[a * (size_t)M + k] = R[0][a] * d[0] + R[1][a] * d[1] + R[2][a] * d[2];
+      }
+    }
+    double* dref = nullptr;
+    if ((rc = upload<double>(h, h->marker_mem, &dref, ref.data(), ref.size()))) return rc;
+    h->m.ref = dref;
+  }
+  // body table
+  std::vector<BodyDev> bd(std::max(n_bodies, 1));
+  for (int b = 0; b < n_bodies; ++b) {
+    const ibm_lbm_body& B = bodies[b];
+    BodyDev& D = bd[b];
+    D.kind = B.kind;
+    D.first = (int)B.first;
+    D.count = (int)B.count;
+    D.kBT_p = (float)B.kBT_p; D.k_b = (float)B.k_b; D.k_l = (float)B.k_l; D.k_g = (float)B.k_g; D.k_v = (float)B.k_v;
+    D.kappa = B.kappa; D.mass = B.mass;
+    for (int a = 0; a < 3; ++a) {
+      D.inertia[a] = B.inertia[a]; D.center[a] = B.center[a]; D.vel[a] = B.vel[a]; D.omega[a] = B.omega[a];
+    }
+    for (int a = 0; a < 4; ++a) D.quat[a] = B.quat[a];
+    h->h_bodies.push_back(B);
+  }
+  if ((rc = upload<BodyDev>(h, h->marker_mem, &h->d_bodies, bd.data(), bd.size()))) return rc;
+  h->n_bodies = n_bodies;
+  // mesh
+  if (any_membrane) {
+    int4* de; float2* dr; int4* dt; float* da;
+    if ((rc = upload<int4>(h, h->marker_mem, &de, hm.edges.data(), hm.edges.size()))) return rc;
+    if ((rc = upload<float2>(h, h->marker_mem, &dr, hm.edge_rest.data(), hm.edge_rest.size()))) return rc;
+    if ((rc = upload<int4>(h, h->marker_mem, &dt, hm.tris.data(), hm.tris.size()))) return rc;
+    if ((rc = upload<float>(h, h->marker_mem, &da, hm.area0.data(), hm.area0.size()))) return rc;
+    h->mesh.nv = mesh->n_vertices;
+    h->mesh.nt = mesh->n_triangles;
+    h->mesh.ne = (int)hm.edges.size();
+    h->mesh.edges = de; h->mesh.edge_rest = dr; h->mesh.tris = dt; h->mesh.tri_area0 = da;
+    h->mesh.A0 = (float)hm.A0;
+    h->mesh.V0 = (float)hm.V0;
+  }
+  h->need_zero_F = covered < n_markers;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_step_async(ibm_lbm_t* h, int64_t n_steps) {
+  if (!h) return IBM_LBM_E_ARG;
+  return enqueue_steps(h, n_steps);
+}
+
+int ibm_lbm_synchronize(ibm_lbm_t* h) {
+  if (!h) return IBM_LBM_E_ARG;
+  return finish_diagnostics(h);
+}
+
+int ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps) {
+  if (!h) return IBM_LBM_E_ARG;
+  int rc = enqueue_steps(h, n_steps);
+  if (rc) return rc;
+  return finish_diagnostics(h);
+}
+
+int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
+  if (!h) return IBM_LBM_E_ARG;
+  cudaStream_t st = h->stream;
+  switch (stage) {
+    case IBM_LBM_STAGE_FORCES:
+      if (h->m.M > 0) {
+        if (h->need_zero_F) CUDA_TRY(h, cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st));
+        launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
+      }
+      break;
+    case IBM_LBM_STAGE_SPREAD:
+      CUDA_TRY(h, cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st));
+      launch_spread(h->L, h->m, st);
+      break;
+    case IBM_LBM_STAGE_COLLIDE:
+      launch_collide(h->L, h->cfg.storage, h->odd_next, true, st);
+      h->odd_next = !h->odd_next;
+      break;
+    case IBM_LBM_STAGE_INTERP:
+      launch_interpolate(h->L, h->m, st);
+      h->steps += 1;
+      break;
+    default:
+      return fail(h, IBM_LBM_E_ARG, "unknown stage");
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F) {
+  if (!h || (!F && h->m.M > 0)) return fail(h, IBM_LBM_E_ARG, "null argument");
+  const size_t M = (size_t)h->m.M;
+  std::vector<float4> tmp(M);
+  for (size_t k = 0; k < M; ++k) tmp[k] = make_float4((float)F[k], (float)F[M + k], (float)F[2 * M + k], 0.f);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (M) CUDA_TRY(h, cudaMemcpy(h->m.F, tmp.data(), sizeof(float4) * M, cudaMemcpyHostToDevice));
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
+  if (!h || !g) return fail(h, IBM_LBM_E_ARG, "null argument");
+  const size_t N = (size_t)h->L.N;
+  std::vector<float4> tmp(N);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(tmp.data(), h->L.g, sizeof(float4) * N, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i) {
+    g[i] = tmp[i].x; g[N + i] = tmp[i].y; g[2 * N + i] = tmp[i].z;
+  }
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
+  if (!h) return IBM_LBM_E_ARG;
+  const LatticeDev& L = h->L;
+  const size_t N = (size_t)L.N;
+  std::vector<float4> tmp(N);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(tmp.data(), L.uw, sizeof(float4) * N, cudaMemcpyDeviceToHost));
+  for (int z = 0; z < L.nz; ++z)
+    for (int y = 0; y < L.ny; ++y) {
+      const bool fl = fluid_yz(L, y, z);
+      const size_t row = (size_t)L.nx * (y + (size_t)L.ny * z);
+      for (int x = 0; x < L.nx; ++x) {
+        const size_t i = row + x;
+        const float4 v = tmp[i];
+        if (rho) rho[i] = fl ? 1.0 + (double)v.w : 0.0;
+        if (u) {
+          u[i] = fl ? v.x : 0.0;
+          u[N + i] = fl ? v.y : 0.0;
+          u[2 * N + i] = fl ? v.z : 0.0;
+        }
+      }
+    }
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
+  if (!h) return IBM_LBM_E_ARG;
+  const size_t M = (size_t)h->m.M;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (M == 0) return IBM_LBM_OK;
+  if (X) CUDA_TRY(h, cudaMemcpy(X, h->m.X, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost));
+  std::vector<float4> tmp;
+  if (U || F) tmp.resize(M);
+  if (U) {
+    CUDA_TRY(h, cudaMemcpy(tmp.data(), h->m.U, sizeof(float4) * M, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < M; ++k) {
+      U[k] = tmp[k].x; U[M + k] = tmp[k].y; U[2 * M + k] = tmp[k].z;
+    }
+  }
+  if (F) {
+    CUDA_TRY(h, cudaMemcpy(tmp.data(), h->m.F, sizeof(float4) * M, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < M; ++k) {
+      F[k] = tmp[k].x; F[M + k] = tmp[k].y; F[2 * M + k] = tmp[k].z;
+    }
+  }
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
+  if (!h || n_bodies != h->n_bodies || (n_bodies > 0 && !bodies))
+    return fail(h, IBM_LBM_E_ARG, "get_bodies: count mismatch");
+  if (n_bodies == 0) return IBM_LBM_OK;
+  std::vector<BodyDev> bd(n_bodies);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(bd.data(), h->d_bodies, sizeof(BodyDev) * n_bodies, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < n_bodies; ++b) {
+    ibm_lbm_body B = h->h_bodies[b];
+    for (int a = 0; a < 3; ++a) {
+      B.center[a] = bd[b].center[a]; B.vel[a] = bd[b].vel[a]; B.omega[a] = bd[b].omega[a];
+    }
+    for (int a = 0; a < 4; ++a) B.quat[a] = bd[b].quat[a];
+    bodies[b] = B;
+  }
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
+  if (!h || max_steps < 0 || max_steps > (1 << 22)) return fail(h, IBM_LBM_E_ARG, "set_timing: bad step count");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (auto e : h->events) cudaEventDestroy(e);
+  h->events.clear();
+  h->timed_steps = 0;
+  h->timing = max_steps > 0;
+  for (int64_t i = 0; i < 5 * max_steps; ++i) {
+    cudaEvent_t e;
+    CUDA_TRY(h, cudaEventCreate(&e));
+    h->events.push_back(e);
+  }
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_timing(ibm_lbm_t* h, double out[5]) {
+  if (!h || !out) return IBM_LBM_E_ARG;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  for (size_t s = 0; s < h->timed_steps; ++s)
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, h->events[5 * s + k], h->events[5 * s + k + 1]));
+      out[k] += ms;
+    }
+  out[4] = (double)h->timed_steps;
+  h->timed_steps = 0;
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]) {
+  if (!h || !out) return IBM_LBM_E_ARG;
+  int rc = enqueue_diagnostics(h);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->diag_pending = false;
+  float umax2;
+  std::memcpy(&umax2, h->h_umax, sizeof(float));
+  out[0] = h->h_diag[4] + h->h_diag[0];
+  out[1] = h->h_diag[1];
+  out[2] = h->h_diag[2];
+  out[3] = h->h_diag[3];
+  out[4] = std::sqrt((double)umax2);
+  out[5] = (double)h->steps;
+  out[6] = h->h_diag[4];
+  out[7] = 0.0;
+  return IBM_LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,392 @@
+// Lattice-Boltzmann kernels: fused BGK collision + Guo forcing + streaming on
+// a single in-place population array (AA access pattern), and the kernels
+// that initialise, import, export and check that array.
+//
+// Method: Sec. 2.1 of arXiv:1704.04551 — Eq. lbm (stream + BGK collide +
+// force term), Eq. BGKequilibrium (equilibrium), Eq. rho_u (moments with the
+// half-force shift), the Guo term F_i, Eq. viscosity (tau).
+//
+// AA pattern (one array, each cell reads and writes the same 19 slots):
+//   even step: f_i(x) is read from A[x][i]; the post-collision f*_i(x) is
+//              written to A[x][opp(i)] (a bounced value carries the
+//              moving-wall term already);
+//   odd step:  f_i(x) is read from A[x - c_i][opp(i)] (from A[x][i] when
+//              x - c_i is solid); f*_i(x) is written to A[x + c_i][i], or,
+//              when x + c_i is solid, bounced to A[x][opp(i)].
+// After an odd step the array holds f(t+1) in the natural layout.
+// Populations are stored as deviations d_i = f_i - w_i (scaled in FP16/BF16)
+// and all arithmetic is FP32 in deviation form, which keeps the O(u)
+// information of f_i ~ w_i in the significand.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibm {
+
+namespace {
+
+template <int S>
+struct Pop {
+  using St = Store<S>;
+  using T = typename St::T;
+  __device__ static __forceinline__ float ld(const T* p, int i) {
+    if constexpr (S == STORE_F32) return *p;
+    else if constexpr (S == STORE_F16) return __half2float(*p) * (1.0f / dev_scale(i));
+    else return __bfloat162float(*p) * (1.0f / dev_scale(i));
+  }
+  __device__ static __forceinline__ void st(T* p, int i, float v) {
+    if constexpr (S == STORE_F32) *p = v;
+    else if constexpr (S == STORE_F16) *p = __float2half_rn(v * dev_scale(i));
+    else *p = __float2bfloat16_rn(v * dev_scale(i));
+  }
+};
+
+struct Cell {
+  int x, y, z;
+  unsigned smask;          // bit (cy+1)*3 + (cz+1): neighbour in that (y,z) direction is solid
+  int oxp, oxm, oyp, oym, ozp, ozm;  // wrapped element offsets of the six axis neighbours
+};
+
+template <int GEOM>
+__device__ __forceinline__ bool make_cell(const LatticeDev& L, int idx, Cell& c) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  c.x = idx % nx;
+  const int t = idx / nx;
+  c.y = t % ny;
+  c.z = t / ny;
+  c.smask = 0u;
+  if constexpr (GEOM != GEOM_PERIODIC) {
+    if (solid_yz(L, c.y, c.z)) return false;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+        if (solid_yz(L, c.y + dy, c.z + dz)) c.smask |= 1u << ((dy + 1) * 3 + (dz + 1));
+  }
+  c.oxp = (c.x == nx - 1) ? -(nx - 1) : 1;
+  c.oxm = (c.x == 0) ? (nx - 1) : -1;
+  const int sy = nx, sz = nx * ny;
+  c.oyp = (c.y == ny - 1) ? -(ny - 1) * sy : sy;
+  c.oym = (c.y == 0) ? (ny - 1) * sy : -sy;
+  c.ozp = (c.z == nz - 1) ? -(nz - 1) * sz : sz;
+  c.ozm = (c.z == 0) ? (nz - 1) * sz : -sz;
+  return true;
+}
+
+// element offset of the neighbour x + s*c_i
+__device__ __forceinline__ int nb_off(const Cell& c, int i, int s) {
+  const int dx = s * cx(i), dy = s * cy(i), dz = s * cz(i);
+  return (dx > 0 ? c.oxp : (dx < 0 ? c.oxm : 0)) + (dy > 0 ? c.oyp : (dy < 0 ? c.oym : 0)) +
+         (dz > 0 ? c.ozp : (dz < 0 ? c.ozm : 0));
+}
+// is x + s*c_i solid?
+__device__ __forceinline__ bool nb_solid(const Cell& c, int i, int s) {
+  return (c.smask >> ((s * cy(i) + 1) * 3 + (s * cz(i) + 1))) & 1u;
+}
+
+}  // namespace
+
+// Fused collide-stream-force kernel, one thread per cell.
+template <int S, int ODD, int GEOM, bool DENSE>
+__global__ void __launch_bounds__(256) k_collide(LatticeDev L) {
+  using P = Pop<S>;
+  using T = typename P::T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.N) return;
+  Cell c;
+  if (!make_cell<GEOM>(L, idx, c)) return;
+  T* A = reinterpret_cast<T*>(L.pop);
+  const size_t N = (size_t)L.N;
+
+  float d[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (!ODD || i == 0) {
+      d[i] = P::ld(A + i * N + idx, i);
+    } else {
+      const bool sol = (GEOM != GEOM_PERIODIC) && nb_solid(c, i, -1);
+      d[i] = sol ? P::ld(A + i * N + idx, i) : P::ld(A + opp(i) * N + (idx + nb_off(c, i, -1)), opp(i));
+    }
+  }
+
+  // moments (Eq. rho_u): rho = sum f, rho u = sum f c + g/2
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += d[i];
+    if (cx(i)) jx += cx(i) * d[i];
+    if (cy(i)) jy += cy(i) * d[i];
+    if (cz(i)) jz += cz(i) * d[i];
+  }
+  float Gx = L.g0x, Gy = L.g0y, Gz = L.g0z;
+  const int tile = (c.x >> TILE_X_SHIFT) + L.ntx * ((c.y >> TILE_Y_SHIFT) + L.nty * (c.z >> TILE_Z_SHIFT));
+  const bool touched = L.flags[tile] != 0;
+  if (touched) {
+    const float4 gg = L.g[idx];
+    Gx += gg.x; Gy += gg.y; Gz += gg.z;
+    L.g[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float rho = 1.0f + drho;
+  const float irho = 1.0f / rho;
+  const float ux = (jx + 0.5f * Gx) * irho;
+  const float uy = (jy + 0.5f * Gy) * irho;
+  const float uz = (jz + 0.5f * Gz) * irho;
+  if (DENSE || touched) L.uw[idx] = make_float4(ux, uy, uz, drho);
+
+  // BGK relaxation toward the equilibrium (Eq. BGKequilibrium) plus the Guo term
+  const float om = L.omega, pre = L.guo_pre;
+  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const float uG = ux * Gx + uy * Gy + uz * Gz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float w = wgt(i);
+    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float cG = cx(i) * Gx + cy(i) * Gy + cz(i) * Gz;
+    const float deq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
+    const float Fi = pre * w * (3.0f * (cG - uG) + 9.0f * cu * cG);
+    d[i] = d[i] + om * (deq - d[i]) + Fi;
+  }
+
+  // streaming with half-way bounce-back (moving-wall term on y walls)
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float v = d[i];
+    bool sol = false;
+    if (GEOM != GEOM_PERIODIC && i != 0) {
+      sol = nb_solid(c, i, +1);
+      if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
+        const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
+        v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
+      }
+    }
+    if (!ODD || i == 0 || sol) {
+      P::st(A + opp(i) * N + idx, opp(i), v);
+    } else {
+      P::st(A + i * N + (idx + nb_off(c, i, +1)), i, v);
+    }
+  }
+}
+
+// Equilibrium initialisation from the moments in uw (ux, uy, uz, rho - 1).
+template <int S, int GEOM>
+__global__ void k_init_equilibrium(LatticeDev L) {
+  using P = Pop<S>;
+  using T = typename P::T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.N) return;
+  Cell c;
+  T* A = reinterpret_cast<T*>(L.pop);
+  const size_t N = (size_t)L.N;
+  if (!make_cell<GEOM>(L, idx, c)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) P::st(A + i * N + idx, i, 0.f);
+    L.uw[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float4 m = L.uw[idx];
+  const float rho = 1.0f + m.w;
+  const float usq15 = 1.5f * (m.x * m.x + m.y * m.y + m.z * m.z);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cu = cx(i) * m.x + cy(i) * m.y + cz(i) * m.z;
+    P::st(A + i * N + idx, i, wgt(i) * (m.w + rho * (3.0f * cu + 4.5f * cu * cu - usq15)));
+  }
+}
+
+// Natural-layout populations f_i = w_i + d_i, FP64 [19][N]; ODD_NEXT = the
+// array is in the post-even-step layout.
+template <int S, int GEOM, bool ODD_NEXT>
+__global__ void k_export(LatticeDev L, double* out) {
+  using P = Pop<S>;
+  using T = typename P::T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.N) return;
+  const T* A = reinterpret_cast<const T*>(L.pop);
+  const size_t N = (size_t)L.N;
+  Cell c;
+  if (!make_cell<GEOM>(L, idx, c)) {
+    for (int i = 0; i < Q; ++i) out[i * N + idx] = 0.0;
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float d;
+    if (!ODD_NEXT || i == 0) {
+      d = P::ld(A + i * N + idx, i);
+    } else {
+      const bool sol = (GEOM != GEOM_PERIODIC) && nb_solid(c, i, -1);
+      d = sol ? P::ld(A + i * N + idx, i) : P::ld(A + opp(i) * N + (idx + nb_off(c, i, -1)), opp(i));
+    }
+    out[i * N + idx] = wgt_d(i) + (double)d;
+  }
+}
+
+template <int S>
+__global__ void k_import(LatticeDev L, const double* in) {
+  using P = Pop<S>;
+  using T = typename P::T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.N) return;
+  T* A = reinterpret_cast<T*>(L.pop);
+  const size_t N = (size_t)L.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) P::st(A + i * N + idx, i, (float)(in[i * N + idx] - wgt_d(i)));
+}
+
+// FP64 sums of the last collision's moments over fluid cells, max |u|, and
+// the finiteness check. out: [0] sum(rho - 1), [1..3] sum rho u, [4] number
+// of fluid cells; *umax2_bits: max |u|^2 as float bits (atomicMax on the
+// bits orders non-negative floats).
+template <int GEOM>
+__global__ void __launch_bounds__(256) k_diagnostics(LatticeDev L, double* out, unsigned* umax2_bits) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+  float m2 = 0.f;
+  bool bad = false;
+  if (idx < L.N) {
+    Cell c;
+    if (make_cell<GEOM>(L, idx, c)) {
+      const float4 m = L.uw[idx];
+      const double rho = 1.0 + (double)m.w;
+      s0 = (double)m.w;
+      s1 = rho * m.x; s2 = rho * m.y; s3 = rho * m.z;
+      s4 = 1.0;
+      m2 = m.x * m.x + m.y * m.y + m.z * m.z;
+      bad = !(isfinite(m.x) && isfinite(m.y) && isfinite(m.z) && isfinite(m.w));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  __shared__ double sh[8][5];
+  __shared__ float shm[8];
+  __shared__ int shbad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) shbad = 0;
+  __syncthreads();
+  if (lane == 0) {
+    sh[warp][0] = s0; sh[warp][1] = s1; sh[warp][2] = s2; sh[warp][3] = s3; sh[warp][4] = s4;
+    shm[warp] = m2;
+    if (bad) shbad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    float mm = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a0 += sh[w][0]; a1 += sh[w][1]; a2 += sh[w][2]; a3 += sh[w][3]; a4 += sh[w][4];
+      mm = fmaxf(mm, shm[w]);
+    }
+    atomicAdd(out + 0, a0);
+    atomicAdd(out + 1, a1);
+    atomicAdd(out + 2, a2);
+    atomicAdd(out + 3, a3);
+    atomicAdd(out + 4, a4);
+    if (shbad) {
+      atomicExch(L.status, 1);
+      atomicMax(umax2_bits, 0x7f800000u);  // +inf
+    } else {
+      atomicMax(umax2_bits, __float_as_uint(mm));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+namespace {
+inline unsigned blocks_for(int n) { return (unsigned)((n + 255) / 256); }
+
+template <int S, int GEOM>
+void launch_collide_g(const LatticeDev& L, bool odd, bool dense, cudaStream_t st) {
+  const unsigned nb = blocks_for(L.N);
+  if (odd) {
+    if (dense) k_collide<S, 1, GEOM, true><<<nb, 256, 0, st>>>(L);
+    else k_collide<S, 1, GEOM, false><<<nb, 256, 0, st>>>(L);
+  } else {
+    if (dense) k_collide<S, 0, GEOM, true><<<nb, 256, 0, st>>>(L);
+    else k_collide<S, 0, GEOM, false><<<nb, 256, 0, st>>>(L);
+  }
+}
+template <int S>
+void launch_collide_s(const LatticeDev& L, bool odd, bool dense, cudaStream_t st) {
+  switch (L.geometry) {
+    case GEOM_PERIODIC: launch_collide_g<S, GEOM_PERIODIC>(L, odd, dense, st); break;
+    case GEOM_YWALLS: launch_collide_g<S, GEOM_YWALLS>(L, odd, dense, st); break;
+    default: launch_collide_g<S, GEOM_TUBE>(L, odd, dense, st); break;
+  }
+}
+template <int S, int GEOM>
+void launch_init_g(const LatticeDev& L, cudaStream_t st) {
+  k_init_equilibrium<S, GEOM><<<blocks_for(L.N), 256, 0, st>>>(L);
+}
+template <int S>
+void launch_init_s(const LatticeDev& L, cudaStream_t st) {
+  switch (L.geometry) {
+    case GEOM_PERIODIC: launch_init_g<S, GEOM_PERIODIC>(L, st); break;
+    case GEOM_YWALLS: launch_init_g<S, GEOM_YWALLS>(L, st); break;
+    default: launch_init_g<S, GEOM_TUBE>(L, st); break;
+  }
+}
+template <int S, int GEOM>
+void launch_export_g(const LatticeDev& L, bool odd_next, double* out, cudaStream_t st) {
+  if (odd_next) k_export<S, GEOM, true><<<blocks_for(L.N), 256, 0, st>>>(L, out);
+  else k_export<S, GEOM, false><<<blocks_for(L.N), 256, 0, st>>>(L, out);
+}
+template <int S>
+void launch_export_s(const LatticeDev& L, bool odd_next, double* out, cudaStream_t st) {
+  switch (L.geometry) {
+    case GEOM_PERIODIC: launch_export_g<S, GEOM_PERIODIC>(L, odd_next, out, st); break;
+    case GEOM_YWALLS: launch_export_g<S, GEOM_YWALLS>(L, odd_next, out, st); break;
+    default: launch_export_g<S, GEOM_TUBE>(L, odd_next, out, st); break;
+  }
+}
+}  // namespace
+
+void launch_collide(const LatticeDev& L, int storage, bool odd, bool dense, cudaStream_t st) {
+  switch (storage) {
+    case STORE_F32: launch_collide_s<STORE_F32>(L, odd, dense, st); break;
+    case STORE_F16: launch_collide_s<STORE_F16>(L, odd, dense, st); break;
+    default: launch_collide_s<STORE_BF16>(L, odd, dense, st); break;
+  }
+}
+
+void launch_init_equilibrium(const LatticeDev& L, int storage, cudaStream_t st) {
+  switch (storage) {
+    case STORE_F32: launch_init_s<STORE_F32>(L, st); break;
+    case STORE_F16: launch_init_s<STORE_F16>(L, st); break;
+    default: launch_init_s<STORE_BF16>(L, st); break;
+  }
+}
+
+void launch_export(const LatticeDev& L, int storage, bool odd_next, double* out, cudaStream_t st) {
+  switch (storage) {
+    case STORE_F32: launch_export_s<STORE_F32>(L, odd_next, out, st); break;
+    case STORE_F16: launch_export_s<STORE_F16>(L, odd_next, out, st); break;
+    default: launch_export_s<STORE_BF16>(L, odd_next, out, st); break;
+  }
+}
+
+void launch_import(const LatticeDev& L, int storage, const double* in, cudaStream_t st) {
+  switch (storage) {
+    case STORE_F32: k_import<STORE_F32><<<blocks_for(L.N), 256, 0, st>>>(L, in); break;
+    case STORE_F16: k_import<STORE_F16><<<blocks_for(L.N), 256, 0, st>>>(L, in); break;
+    default: k_import<STORE_BF16><<<blocks_for(L.N), 256, 0, st>>>(L, in); break;
+  }
+}
+
+void launch_diagnostics(const LatticeDev& L, double* out, unsigned* umax2_bits, cudaStream_t st) {
+  switch (L.geometry) {
+    case GEOM_PERIODIC: k_diagnostics<GEOM_PERIODIC><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
+    case GEOM_YWALLS: k_diagnostics<GEOM_YWALLS><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
+    default: k_diagnostics<GEOM_TUBE><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
+  }
+}
+
+}  // namespace ibm

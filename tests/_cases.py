@@ -1,0 +1,48 @@
+"""Small seeded cases shared by the GPU parity tests (sizes the FP64 oracle
+finishes in seconds, spanning several 32-wide x tiles plus a ragged tail)."""
+import numpy as np
+
+from paper_1704_04551_gb300 import inputs as I
+
+LATTICES = {
+    'periodic': dict(nx=40, ny=12, nz=10, tau=0.8, geometry=0, body_force=[2e-6, -1e-6, 5e-7]),
+    'ywalls': dict(nx=40, ny=11, nz=9, tau=0.7, geometry=1, wall_u=[-0.015, 0.02], body_force=[1e-6, 0, 0]),
+    'tube': dict(nx=37, ny=14, nz=13, tau=1.0, geometry=2, tube_radius=5.6, body_force=[3e-6, 0, 0]),
+}
+
+
+def shape(lat):
+    return (lat['nx'], lat['ny'], lat['nz'])
+
+
+def fluid_mask(lat):
+    nx, ny, nz = shape(lat)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing='ij')
+    if lat['geometry'] == 2:
+        yc, zc = (ny - 1) / 2, (nz - 1) / 2
+        m = (y - yc) ** 2 + (z - zc) ** 2 <= lat['tube_radius'] ** 2
+    else:
+        m = np.ones_like(x, dtype=bool)
+    return m.ravel()
+
+
+def markers_inside(lat, M, seed):
+    """Random marker positions in the fluid (some within 2 lu of walls,
+    some across periodic boundaries)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape(lat)
+    if lat['geometry'] == 2:
+        r = (lat['tube_radius'] - 0.5) * np.sqrt(rng.random(M))
+        th = 2 * np.pi * rng.random(M)
+        return np.stack([nx * rng.random(M) - 0.5 * nx * (rng.random(M) < 0.1),
+                         (ny - 1) / 2 + r * np.cos(th), (nz - 1) / 2 + r * np.sin(th)])
+    X = np.stack([nx * rng.random(M), (ny - 1) * rng.random(M), nz * rng.random(M)])
+    X[0, : M // 10] += nx * 2.0  # unwrapped positions beyond the box
+    X[2, : M // 10] -= nz
+    if lat['geometry'] == 0:
+        X[1, : M // 10] -= ny
+    return X
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

@@ -11,3 +11,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line('markers', 'gpu: needs a CUDA GPU (sm_103a) and the built CUDA library')
     config.addinivalue_line('markers', 'slow: long-running CPU test')
+
+
+@pytest.fixture(scope='session')
+def cuda_lib():
+    """Build (if needed) and load the CUDA library; GPU tests only."""
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1704_04551_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding

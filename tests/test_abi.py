@@ -1,0 +1,48 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/ibm_lbm.h declares (no compute calls)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_1704_04551_gb300 import binding, build
+
+
+@pytest.fixture(scope='module')
+def libpath():
+    return build.build()
+
+
+def test_header_declares_the_boundary(libpath):
+    names = binding.exported_symbols()
+    for required in ('ibm_lbm_create', 'ibm_lbm_destroy', 'ibm_lbm_set_lattice', 'ibm_lbm_set_markers',
+                     'ibm_lbm_step', 'ibm_lbm_get_fields', 'ibm_lbm_get_markers'):
+        assert required in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in binding.exported_symbols():
+        assert hasattr(lib, name), name
+    out = subprocess.run(['nm', '-D', '--defined-only', libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in binding.exported_symbols():
+        assert name in exported, name
+
+
+def test_binding_signatures_load(libpath):
+    L = binding.load()
+    assert binding.ibm_lbm_version().startswith('ibm_lbm')
+    assert L.ibm_lbm_last_error(None) == b'null handle'
+    # invalid configs are rejected before any device work
+    cfg = binding.Config()
+    cfg.nx = cfg.ny = cfg.nz = 2
+    cfg.tau = 0.8
+    out = ctypes.c_void_p()
+    assert L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == binding.E_ARG
+    cfg.nx = cfg.ny = cfg.nz = 8
+    cfg.tau = 0.4
+    assert L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == binding.E_ARG
+    assert L.ibm_lbm_destroy(None) == 0
