@@ -201,6 +201,36 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
 int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps);
 int ibm_lbm_get_timing(ibm_lbm_t* h, double out[5]);
 
+/* Force spreading for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment helper. Some callers
+ * cannot call cudaMalloc at all, for example a host framework that has
+ * already reserved the GPU's memory for its own pool and forbids further
+ * allocations, or a time-critical loop that may not pay allocation latency
+ * or synchronisation. This entry point spreads marker forces to the lattice
+ * (the same operation as the SPREAD stage of a handle) without a handle and
+ * without allocating: it accumulates into a fixed, file-scope device array
+ * of IBM_LBM_NOALLOC_MAX_CELLS float4 values (16 MiB), which every GPU that
+ * loads this library holds until the process exits.
+ *
+ * Inputs (device pointers owned by the caller): X [3][M] FP64 marker
+ * positions, F [3][M] FP64 marker forces. Output: g [3][N] FP64 force
+ * density, N = nx*ny*nz, fully overwritten (cells outside every stencil get
+ * 0). geometry / tube_radius as in ibm_lbm_config; stream is a cudaStream_t
+ * or NULL. The call only enqueues work on the stream and returns; g is ready
+ * when the stream reaches that point.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * Every call shares the one array per device and clears it first, so calls
+ * whose work overlaps on the GPU (different streams, host threads) race and
+ * must be serialised by the caller.
+ * Errors: IBM_LBM_E_ARG if nx*ny*nz > IBM_LBM_NOALLOC_MAX_CELLS, any
+ * dimension < 4, M < 0, a null pointer with M > 0 or N > 0, or an unknown
+ * geometry; IBM_LBM_E_CUDA if the address lookup or a launch fails. */
+#define IBM_LBM_NOALLOC_MAX_CELLS (1 << 20)
+int ibm_lbm_spread_noalloc(const double* X, const double* F, int64_t n_markers, int32_t nx, int32_t ny,
+                           int32_t nz, int32_t geometry, double tube_radius, double* g, void* stream);
+
 /* The cudaStream_t the handle works on. */
 void* ibm_lbm_stream(ibm_lbm_t* h);
 /* Bytes of device memory the handle holds. */

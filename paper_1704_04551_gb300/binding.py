@@ -90,6 +90,7 @@ def load():
         'ibm_lbm_get_force_density': ([P, P], C.c_int),
         'ibm_lbm_set_timing': ([P, I64], C.c_int),
         'ibm_lbm_get_timing': ([P, P], C.c_int),
+        'ibm_lbm_spread_noalloc': ([P, P, I64, I32, I32, I32, I32, D, P, P], C.c_int),
         'ibm_lbm_stream': ([P], P),
         'ibm_lbm_device_bytes': ([P], C.c_size_t),
         'ibm_lbm_last_error': ([P], C.c_char_p),
@@ -218,6 +219,14 @@ def ibm_lbm_get_timing(h):
     out = np.zeros(5)
     _check(h, load().ibm_lbm_get_timing(h, _p(out)))
     return out
+
+
+def ibm_lbm_spread_noalloc(X_ptr, F_ptr, n_markers, nx, ny, nz, geometry, tube_radius, g_ptr, stream=None):
+    """Spreading without device allocation; all pointers are device
+    addresses owned by the caller (see the header for the contract)."""
+    return load().ibm_lbm_spread_noalloc(C.c_void_p(X_ptr), C.c_void_p(F_ptr), int(n_markers), int(nx), int(ny),
+                                         int(nz), int(geometry), float(tube_radius), C.c_void_p(g_ptr),
+                                         C.c_void_p(stream) if stream else None)
 
 
 def ibm_lbm_stream(h):
