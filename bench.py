@@ -54,6 +54,12 @@ def make_workload(name: str):
         w['storage'] = {'tube256': 'f32', 'tube256_f16': 'f16', 'tube256_bf16': 'bf16'}[name]
         w['label'] = f'rbc_tube_256^3_R120_3000x642_{w["storage"]}'
         return w
+    if name == 'tube160':
+        # same cell density and Re as the 256^3 case, for detailed profiles
+        w = I.rbc_tube(n=160, radius=75.0, n_cells=732, seed=1706, steps=200)
+        w['storage'] = 'f32'
+        w['label'] = 'rbc_tube_160^3_R75_732x642_f32'
+        return w
     if name == 'tube64':
         w = I.rbc_tube(n=64, radius=30.0, n_cells=50, seed=1707, steps=1000)
         w['storage'] = 'f32'
@@ -381,6 +387,9 @@ def run_ours(args):
     if rank == 0:
         tot = sum(stages[k] for k in ('forces_ms', 'spread_ms', 'collide_ms', 'interp_ms'))
         split = {k: stages[k] / max(1, stages['steps']) for k in ('forces_ms', 'spread_ms', 'collide_ms', 'interp_ms')}
+        half = max(1, stages['steps']) / 2
+        split['collide_even_ms'] = (stages['collide_ms'] - stages['collide_odd_ms']) / half
+        split['collide_odd_ms'] = stages['collide_odd_ms'] / half
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms_max / args.steps, higher_is_better=True, scaling='weak', vs_baseline=None,
@@ -391,7 +400,7 @@ def run_ours(args):
                         mflups_fluid=Nf * args.steps * ws / (ms_max / 1e3) / 1e6,
                         graph_path_ms_per_step=graph_ms / args.steps,
                         stage_ms_per_step=split,
-                        coupling_share=(split['spread_ms'] + split['interp_ms']) / max(1e-12, sum(split.values())),
+                        coupling_share=(split['spread_ms'] + split['interp_ms']) / max(1e-12, tot / max(1, stages['steps'])),
                         l2='inputs larger than L2 (populations %.2f GB)' % (19 * N * sp / 1e9),
                         parallelism=f'replicas x{ws}' if ws > 1 else 'single GPU'),
             roofline=roof, cpu_baseline=cpu, e2e=e2e,
@@ -413,7 +422,7 @@ def main(argv=None):
     ap.add_argument('--steps', type=int, default=1000)
     ap.add_argument('--warmup', type=int, default=20)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--workload', default='tube256', choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube64', 'shear32'])
+    ap.add_argument('--workload', default='tube256', choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube160', 'tube64', 'shear32'])
     ap.add_argument('--storage', default=None, choices=[None, 'f32', 'f16', 'bf16'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--ref-max-steps', type=int, default=2)

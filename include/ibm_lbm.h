@@ -115,7 +115,9 @@ typedef struct {
  * triangle mesh. Rest edge lengths, rest dihedral angles, rest triangle
  * areas, rest total area and volume are taken from rest_X. */
 typedef struct {
-  int32_t n_vertices;      /* <= 4096 */
+  int32_t n_vertices;      /* <= 4096, and 24 B per vertex + 16 B per triangle + 8 B per
+                              edge must fit one thread block's shared memory (about
+                              2800 vertices for a closed triangulation) */
   int32_t n_triangles;
   const int32_t* tris;     /* host [n_triangles][3], counter-clockwise seen from outside */
   const double* rest_X;    /* host [3][n_vertices] */
@@ -148,7 +150,7 @@ int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
  * no body is a membrane. X: host [3][n_markers]. Markers outside every
  * body are passive tracers (zero force). Errors: E_ARG (overlapping or
  * out-of-range bodies, membrane count != n_vertices, non-manifold mesh,
- * n_vertices > 4096), E_NOMEM. */
+ * template too large), E_NOMEM. */
 int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
                         const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
 
@@ -197,9 +199,10 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
  * n = 0 turns timing off. ibm_lbm_get_timing waits for the stream and
  * returns, summed over the timed steps, the milliseconds of out[0] marker
  * forces, out[1] spreading, out[2] collide-stream, out[3] interpolation,
- * and out[4] = number of timed steps; then resets the sums. */
+ * out[4] = number of timed steps, out[5] = the part of out[2] spent in
+ * odd (neighbour-addressed) AA steps; then resets the sums. */
 int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps);
-int ibm_lbm_get_timing(ibm_lbm_t* h, double out[5]);
+int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]);
 
 /* Force spreading for callers that cannot allocate device memory.
  *

@@ -18,7 +18,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, 'libibmlbm.so')
+LIB_PATH = os.environ.get('IBM_LBM_LIBRARY') or os.path.join(_HERE, 'libibmlbm.so')
 
 OK, E_ARG, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6
 STORE_F32, STORE_F16_DEV, STORE_BF16_DEV = 0, 1, 2
@@ -216,7 +216,7 @@ def ibm_lbm_set_timing(h, max_steps):
 
 
 def ibm_lbm_get_timing(h):
-    out = np.zeros(5)
+    out = np.zeros(6)
     _check(h, load().ibm_lbm_get_timing(h, _p(out)))
     return out
 
@@ -413,7 +413,8 @@ class Simulation:
 
     def timing(self):
         t = ibm_lbm_get_timing(self.h)
-        return dict(forces_ms=t[0], spread_ms=t[1], collide_ms=t[2], interp_ms=t[3], steps=int(t[4]))
+        return dict(forces_ms=t[0], spread_ms=t[1], collide_ms=t[2], interp_ms=t[3], steps=int(t[4]),
+                    collide_odd_ms=t[5])
 
     @property
     def stream(self):

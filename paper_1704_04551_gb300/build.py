@@ -38,16 +38,20 @@ def _deps():
     return out
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None) -> str:
+    """Compile (if sources are newer) and return the library path. ``out``
+    and ``extra`` build a variant elsewhere with additional nvcc flags."""
+    lib = out or LIB
+    bdir = BUILD if out is None else out + '.build'
+    os.makedirs(bdir, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _deps() + [__file__])
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     cc = nvcc()
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + '.o')
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + '.o')
         objs.append(obj)
         cmds.append([cc, *ARCH, *FLAGS, *extra, '-I', INCLUDE, '-c', src, '-o', obj])
     with cf.ThreadPoolExecutor(max_workers=min(8, len(cmds))) as ex:
@@ -58,13 +62,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f'nvcc failed: {" ".join(c)}')
-    tmp = LIB + f'.{os.getpid()}.tmp'
+    tmp = lib + f'.{os.getpid()}.tmp'
     r = subprocess.run([cc, *ARCH, '-shared', '-o', tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError('link failed')
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == '__main__':

@@ -21,6 +21,8 @@ namespace {
 
 constexpr int CHUNK = 16;          // steps per captured chunk graph (even)
 constexpr int MAX_MESH_VERTICES = 4096;
+constexpr int BODY_GROUP = 1024;   // markers per transfer block within a body
+constexpr int TRACER_GROUP = 256;  // markers per transfer block for passive tracers
 
 struct Alloc {
   void* p;
@@ -35,7 +37,11 @@ struct ibm_lbm {
   bool has_alloc = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  LatticeDev L{};
+  LatticeDev L{};                 // g / flags fields unused: see lat()
+  float4* gbuf[2] = {nullptr, nullptr};   // force density, by step parity
+  uint8_t* fbuf[2] = {nullptr, nullptr};  // touched-tile flags, by step parity
+  RowInfo* rows = nullptr;        // fluid rows of the lattice
+  int n_rows = 0;
   std::vector<Alloc> lattice_mem, marker_mem;
   size_t bytes = 0;
   // markers
@@ -44,6 +50,14 @@ struct ibm_lbm {
   BodyDev* d_bodies = nullptr;
   std::vector<ibm_lbm_body> h_bodies;
   MeshDev mesh{};
+  int* membrane_list = nullptr;   // body indices of membranes / rigid bodies
+  int* rigid_list = nullptr;
+  int n_membranes = 0, n_rigids = 0;
+  bool persistent_forces = false;
+  int n_sm = 0;
+  MarkerGroup* groups = nullptr;  // transfer blocks
+  int n_groups = 0;
+  int4* boxes = nullptr;          // per group: stencil box origin and size
   bool need_zero_F = false;
   // state
   long long steps = 0;
@@ -56,6 +70,7 @@ struct ibm_lbm {
   bool diag_pending = false;
   // per-stage timing (events between stages, direct launches)
   std::vector<cudaEvent_t> events;  // 5 per timed step
+  std::vector<char> timed_odd;      // AA parity of each timed step
   size_t timed_steps = 0;
   bool timing = false;
   // graphs
@@ -115,17 +130,30 @@ void drop_graphs(ibm_lbm_t* h) {
 
 int tiles(const LatticeDev& L) { return L.ntx * L.nty * L.ntz; }
 
+// Lattice view for a step of the given AA parity: that step spreads into and
+// reads gbuf[odd] / fbuf[odd] and clears gbuf[!odd] where fbuf[!odd] is set.
+LatticeDev lat(const ibm_lbm_t* h, bool odd) {
+  LatticeDev L = h->L;
+  L.g = h->gbuf[odd ? 1 : 0];
+  L.flags = h->fbuf[odd ? 1 : 0];
+  L.g_next = h->gbuf[odd ? 0 : 1];
+  L.flags_next = h->fbuf[odd ? 0 : 1];
+  return L;
+}
+
 // One coupled step on the handle's stream (also used under capture).
 void enqueue_step(ibm_lbm_t* h, bool odd, bool dense) {
   cudaStream_t st = h->stream;
-  cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st);
+  const LatticeDev L = lat(h, odd);
+  cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
   if (h->m.M > 0) {
     if (h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
-    launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
-    launch_spread(h->L, h->m, st);
+    launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
+                  h->persistent_forces, h->n_sm, st);
+    launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   }
-  launch_collide(h->L, h->cfg.storage, odd, dense, st);
-  if (h->m.M > 0) launch_interpolate(h->L, h->m, st);
+  launch_collide(L, h->rows, h->n_rows, h->cfg.storage, odd, dense, st);
+  if (h->m.M > 0) launch_interpolate(L, h->m, h->groups, h->n_groups, h->boxes, st);
 }
 
 // One step with an event before each stage and after the last.
@@ -136,18 +164,23 @@ void enqueue_timed_step(ibm_lbm_t* h, bool odd, bool dense) {
   auto mark = [&](int k) {
     if (rec) cudaEventRecord(h->events[base + k], st);
   };
-  cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st);
+  const LatticeDev L = lat(h, odd);
+  cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
   if (h->m.M > 0 && h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
   mark(0);
-  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
+  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
+                  h->persistent_forces, h->n_sm, st);
   mark(1);
-  if (h->m.M > 0) launch_spread(h->L, h->m, st);
+  if (h->m.M > 0) launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   mark(2);
-  launch_collide(h->L, h->cfg.storage, odd, dense, st);
+  launch_collide(L, h->rows, h->n_rows, h->cfg.storage, odd, dense, st);
   mark(3);
-  if (h->m.M > 0) launch_interpolate(h->L, h->m, st);
+  if (h->m.M > 0) launch_interpolate(L, h->m, h->groups, h->n_groups, h->boxes, st);
   mark(4);
-  if (rec) h->timed_steps++;
+  if (rec) {
+    h->timed_odd.push_back(odd ? 1 : 0);
+    h->timed_steps++;
+  }
 }
 
 int capture(ibm_lbm_t* h, cudaGraphExec_t* out, int n, bool odd0, bool dense_last) {
@@ -169,7 +202,7 @@ int enqueue_diagnostics(ibm_lbm_t* h) {
   cudaStream_t st = h->stream;
   CUDA_TRY(h, cudaMemsetAsync(h->d_diag, 0, 8 * sizeof(double), st));
   CUDA_TRY(h, cudaMemsetAsync(h->d_umax, 0, sizeof(unsigned), st));
-  launch_diagnostics(h->L, h->d_diag, h->d_umax, st);
+  launch_diagnostics(h->L, h->rows, h->n_rows, h->d_diag, h->d_umax, st);
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaMemcpyAsync(h->h_diag, h->d_diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_umax, h->d_umax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -233,7 +266,9 @@ int enqueue_steps(ibm_lbm_t* h, int64_t n) {
 // ---- membrane template: edges and rest state (FP64) --------------------------
 struct HostMesh {
   std::vector<int4> edges;
+  std::vector<int2> edge_tris;
   std::vector<float2> edge_rest;
+  std::vector<int> v_edge_start, v_edge, v_tri_start, v_tri;
   std::vector<int4> tris;
   std::vector<float> area0;
   double A0 = 0, V0 = 0;
@@ -255,6 +290,7 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
   auto P = [&](int v) { return V3{mesh->rest_X[v], mesh->rest_X[nv + v], mesh->rest_X[2 * nv + v]}; };
   std::unordered_map<uint64_t, int> emap;
   out.edges.clear();
+  out.edge_tris.clear();
   out.tris.resize(nt);
   for (int t = 0; t < nt; ++t) {
     int v[3] = {mesh->tris[3 * t], mesh->tris[3 * t + 1], mesh->tris[3 * t + 2]};
@@ -271,6 +307,7 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
       if (it == emap.end()) {
         emap.emplace(key, (int)out.edges.size());
         out.edges.push_back(make_int4(a, b, c, -1));
+        out.edge_tris.push_back(make_int2(t, -1));
       } else {
         int4& e = out.edges[it->second];
         if (e.w >= 0 || e.x != b || e.y != a) {
@@ -278,6 +315,7 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
           return false;
         }
         e.w = c;
+        out.edge_tris[it->second].y = t;
       }
     }
   }
@@ -310,6 +348,30 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
     why = "mesh: non-positive rest volume (triangles must be counter-clockwise seen from outside)";
     return false;
   }
+  // per-vertex lists of (edge, role) and (triangle, slot), CSR
+  std::vector<std::vector<int>> ve(nv), vt(nv);
+  for (size_t e = 0; e < out.edges.size(); ++e) {
+    const int4 E = out.edges[e];
+    ve[E.x].push_back((int)(e << 2) | 0);
+    ve[E.y].push_back((int)(e << 2) | 1);
+    ve[E.z].push_back((int)(e << 2) | 2);
+    ve[E.w].push_back((int)(e << 2) | 3);
+  }
+  for (int t = 0; t < nt; ++t) {
+    vt[out.tris[t].x].push_back((t << 2) | 0);
+    vt[out.tris[t].y].push_back((t << 2) | 1);
+    vt[out.tris[t].z].push_back((t << 2) | 2);
+  }
+  out.v_edge_start.assign(1, 0);
+  out.v_tri_start.assign(1, 0);
+  out.v_edge.clear();
+  out.v_tri.clear();
+  for (int v = 0; v < nv; ++v) {
+    out.v_edge.insert(out.v_edge.end(), ve[v].begin(), ve[v].end());
+    out.v_tri.insert(out.v_tri.end(), vt[v].begin(), vt[v].end());
+    out.v_edge_start.push_back((int)out.v_edge.size());
+    out.v_tri_start.push_back((int)out.v_tri.size());
+  }
   return true;
 }
 
@@ -336,6 +398,34 @@ bool fluid_yz(const LatticeDev& L, int y, int z) {
     return !(dy * dy + dz * dz > L.R2);
   }
   return true;
+}
+
+std::vector<RowInfo> build_rows(const LatticeDev& L) {
+  std::vector<RowInfo> rows;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y) {
+      if (!fluid_yz(L, y, z)) continue;
+      RowInfo R{};
+      R.base = nx * (y + ny * z);
+      R.y = y;
+      R.trow = L.ntx * ((y >> TILE_Y_SHIFT) + L.nty * (z >> TILE_Z_SHIFT));
+      R.oyp = (y == ny - 1) ? -(ny - 1) * nx : nx;
+      R.oym = (y == 0) ? (ny - 1) * nx : -nx;
+      R.ozp = (z == nz - 1) ? -(nz - 1) * nx * ny : nx * ny;
+      R.ozm = (z == 0) ? (nz - 1) * nx * ny : -nx * ny;
+      int mask = 0;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          int yy = y + dy, zz = z + dz;
+          if (L.geometry == GEOM_PERIODIC) continue;
+          if (L.geometry == GEOM_YWALLS) zz = (zz + nz) % nz;
+          if (!fluid_yz(L, yy, zz)) mask |= 1 << ((dy + 1) * 3 + (dz + 1));
+        }
+      R.smask = mask;
+      rows.push_back(R);
+    }
+  return rows;
 }
 
 }  // namespace
@@ -397,14 +487,28 @@ int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, vo
   const size_t sp = cfg->storage == STORE_F32 ? 4 : 2;
   L.pop = dalloc(h, h->lattice_mem, (size_t)Q * N * sp);
   L.uw = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
-  L.g = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
-  L.flags = (uint8_t*)dalloc(h, h->lattice_mem, (size_t)tiles(L));
+  for (int p = 0; p < 2; ++p) {
+    h->gbuf[p] = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
+    h->fbuf[p] = (uint8_t*)dalloc(h, h->lattice_mem, (size_t)tiles(L));
+  }
   L.status = (int*)dalloc(h, h->lattice_mem, 256);
   h->d_diag = (double*)dalloc(h, h->lattice_mem, 8 * sizeof(double));
   h->d_umax = (unsigned*)dalloc(h, h->lattice_mem, 256);
-  if (!L.pop || !L.uw || !L.g || !L.flags || !L.status || !h->d_diag || !h->d_umax) {
+  if (!L.pop || !L.uw || !h->gbuf[0] || !h->gbuf[1] || !h->fbuf[0] || !h->fbuf[1] || !L.status || !h->d_diag ||
+      !h->d_umax) {
     h->err = "device allocation failed";
     return bail(IBM_LBM_E_NOMEM);
+  }
+  {
+    std::vector<RowInfo> rows = build_rows(L);
+    h->n_rows = (int)rows.size();
+    if (upload<RowInfo>(h, h->lattice_mem, &h->rows, rows.data(), rows.size())) return bail(IBM_LBM_E_NOMEM);
+  }
+  if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
+    return bail(IBM_LBM_E_CUDA);
+  if (transfer_configure() != cudaSuccess) {
+    cudaGetLastError();
+    return bail(IBM_LBM_E_CUDA);
   }
   if (cudaMallocHost((void**)&h->h_diag, 8 * sizeof(double) + 2 * sizeof(unsigned) + sizeof(int)) != cudaSuccess)
     return bail(IBM_LBM_E_NOMEM);
@@ -445,8 +549,10 @@ int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
   CUDA_TRY(h, cudaMemcpyAsync(L.uw, m.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, h->stream));
   launch_init_equilibrium(L, h->cfg.storage, h->stream);
   CUDA_TRY(h, cudaGetLastError());
-  CUDA_TRY(h, cudaMemsetAsync(L.g, 0, sizeof(float4) * N, h->stream));
-  CUDA_TRY(h, cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), h->stream));
+  for (int p = 0; p < 2; ++p) {
+    CUDA_TRY(h, cudaMemsetAsync(h->gbuf[p], 0, sizeof(float4) * N, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->fbuf[p], 0, (size_t)tiles(L), h->stream));
+  }
   CUDA_TRY(h, cudaMemsetAsync(L.status, 0, sizeof(int), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->steps = 0;
@@ -468,6 +574,12 @@ int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
   }
   release_pool(h, tmp);
   if (rc) return fail(h, rc, "set_populations: CUDA error");
+  // the parity restarts: clear both force-density buffers and their flags
+  for (int p = 0; p < 2; ++p) {
+    CUDA_TRY(h, cudaMemsetAsync(h->gbuf[p], 0, sizeof(float4) * (size_t)h->L.N, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->fbuf[p], 0, (size_t)tiles(h->L), h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->odd_next = false;
   return IBM_LBM_OK;
 }
@@ -502,6 +614,12 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   h->d_bodies = nullptr;
   h->h_bodies.clear();
   h->mesh = MeshDev{};
+  h->membrane_list = h->rigid_list = nullptr;
+  h->n_membranes = h->n_rigids = 0;
+  h->persistent_forces = false;
+  h->groups = nullptr;
+  h->n_groups = 0;
+  h->boxes = nullptr;
   const int M = (int)n_markers;
   // validate bodies
   std::vector<std::pair<int64_t, int64_t>> ranges;
@@ -533,8 +651,8 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   if (any_membrane) {
     std::string why;
     if (!build_mesh(mesh, hm, why)) return fail(h, IBM_LBM_E_ARG, why);
-    const size_t smem = forces_smem_bytes(mesh->n_vertices);
-    if (smem > 48 * 1024) CUDA_TRY(h, forces_configure(smem));
+    if (hm.edges.size() >= 16384 || (size_t)mesh->n_triangles >= 16384)
+      return fail(h, IBM_LBM_E_ARG, "set_markers: membrane template has too many edges or triangles");
   }
   int rc;
   // marker arrays
@@ -580,19 +698,80 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   }
   if ((rc = upload<BodyDev>(h, h->marker_mem, &h->d_bodies, bd.data(), bd.size()))) return rc;
   h->n_bodies = n_bodies;
+  {
+    std::vector<int> mem, rig;
+    for (int b = 0; b < n_bodies; ++b) (bodies[b].kind == IBM_LBM_BODY_MEMBRANE ? mem : rig).push_back(b);
+    h->n_membranes = (int)mem.size();
+    h->n_rigids = (int)rig.size();
+    if ((rc = upload<int>(h, h->marker_mem, &h->membrane_list, mem.data(), mem.size()))) return rc;
+    if ((rc = upload<int>(h, h->marker_mem, &h->rigid_list, rig.data(), rig.size()))) return rc;
+  }
   // mesh
   if (any_membrane) {
-    int4* de; float2* dr; int4* dt; float* da;
-    if ((rc = upload<int4>(h, h->marker_mem, &de, hm.edges.data(), hm.edges.size()))) return rc;
-    if ((rc = upload<float2>(h, h->marker_mem, &dr, hm.edge_rest.data(), hm.edge_rest.size()))) return rc;
-    if ((rc = upload<int4>(h, h->marker_mem, &dt, hm.tris.data(), hm.tris.size()))) return rc;
-    if ((rc = upload<float>(h, h->marker_mem, &da, hm.area0.data(), hm.area0.size()))) return rc;
-    h->mesh.nv = mesh->n_vertices;
-    h->mesh.nt = mesh->n_triangles;
-    h->mesh.ne = (int)hm.edges.size();
-    h->mesh.edges = de; h->mesh.edge_rest = dr; h->mesh.tris = dt; h->mesh.tri_area0 = da;
-    h->mesh.A0 = (float)hm.A0;
-    h->mesh.V0 = (float)hm.V0;
+    // pack the topology into 16-byte-aligned sections of one buffer
+    std::vector<unsigned char> buf;
+    auto section = [&](const void* src, size_t bytes) {
+      const int off = (int)buf.size();
+      buf.resize(buf.size() + ((bytes + 15) / 16) * 16, 0);
+      if (bytes) std::memcpy(buf.data() + off, src, bytes);
+      return off;
+    };
+    std::vector<ushort4> e16(hm.edges.size());
+    std::vector<ushort2> et16(hm.edges.size());
+    for (size_t e = 0; e < hm.edges.size(); ++e) {
+      e16[e] = make_ushort4(hm.edges[e].x, hm.edges[e].y, hm.edges[e].z, hm.edges[e].w);
+      et16[e] = make_ushort2(hm.edge_tris[e].x, hm.edge_tris[e].y);
+    }
+    std::vector<ushort4> t16(hm.tris.size());
+    for (size_t t = 0; t < hm.tris.size(); ++t) t16[t] = make_ushort4(hm.tris[t].x, hm.tris[t].y, hm.tris[t].z, 0);
+    auto to16 = [](const std::vector<int>& v) { return std::vector<unsigned short>(v.begin(), v.end()); };
+    const auto ves = to16(hm.v_edge_start), vel = to16(hm.v_edge), vts = to16(hm.v_tri_start), vtl = to16(hm.v_tri);
+    MeshDev& D = h->mesh;
+    D.off_edges = section(e16.data(), e16.size() * sizeof(ushort4));
+    D.off_edge_tris = section(et16.data(), et16.size() * sizeof(ushort2));
+    D.off_edge_rest = section(hm.edge_rest.data(), hm.edge_rest.size() * sizeof(float2));
+    D.off_tris = section(t16.data(), t16.size() * sizeof(ushort4));
+    D.off_area0 = section(hm.area0.data(), hm.area0.size() * sizeof(float));
+    D.off_ve_start = section(ves.data(), ves.size() * 2);
+    D.off_ve = section(vel.data(), vel.size() * 2);
+    D.off_vt_start = section(vts.data(), vts.size() * 2);
+    D.off_vt = section(vtl.data(), vtl.size() * 2);
+    D.packed_bytes = (int)buf.size();
+    unsigned char* dpk = nullptr;
+    if ((rc = upload<unsigned char>(h, h->marker_mem, &dpk, buf.data(), buf.size()))) return rc;
+    D.packed = dpk;
+    D.nv = mesh->n_vertices;
+    D.nt = mesh->n_triangles;
+    D.ne = (int)hm.edges.size();
+    D.work_floats = (int)membrane_work_floats(D.nv, D.nt, D.ne);
+    D.A0 = (float)hm.A0;
+    D.V0 = (float)hm.V0;
+    int dev = 0, optin = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (forces_configure(D, (size_t)optin, &h->persistent_forces) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, IBM_LBM_E_ARG, "set_markers: membrane template too large for one thread block's shared memory");
+    }
+  }
+  // transfer groups: bodies in chunks of BODY_GROUP, tracer runs in chunks of TRACER_GROUP
+  {
+    std::vector<MarkerGroup> groups;
+    std::vector<std::pair<int64_t, int64_t>> cuts = ranges;  // sorted body ranges
+    int64_t pos = 0;
+    auto add_run = [&](int64_t a, int64_t b, int step) {
+      for (int64_t s0 = a; s0 < b; s0 += step) groups.push_back({(int)s0, (int)std::min<int64_t>(step, b - s0)});
+    };
+    for (auto& r : cuts) {
+      add_run(pos, r.first, TRACER_GROUP);
+      add_run(r.first, r.second, BODY_GROUP);
+      pos = r.second;
+    }
+    add_run(pos, n_markers, TRACER_GROUP);
+    h->n_groups = (int)groups.size();
+    if ((rc = upload<MarkerGroup>(h, h->marker_mem, &h->groups, groups.data(), groups.size()))) return rc;
+    h->boxes = (int4*)dalloc(h, h->marker_mem, sizeof(int4) * 2 * std::max<size_t>(1, groups.size()));
+    if (!h->boxes) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
   }
   h->need_zero_F = covered < n_markers;
   return IBM_LBM_OK;
@@ -622,19 +801,22 @@ int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
     case IBM_LBM_STAGE_FORCES:
       if (h->m.M > 0) {
         if (h->need_zero_F) CUDA_TRY(h, cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st));
-        launch_forces(h->m, h->d_bodies, h->n_bodies, h->mesh, st);
+        launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
+                  h->persistent_forces, h->n_sm, st);
       }
       break;
-    case IBM_LBM_STAGE_SPREAD:
-      CUDA_TRY(h, cudaMemsetAsync(h->L.flags, 0, (size_t)tiles(h->L), st));
-      launch_spread(h->L, h->m, st);
+    case IBM_LBM_STAGE_SPREAD: {
+      const LatticeDev L = lat(h, h->odd_next);
+      CUDA_TRY(h, cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st));
+      launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
       break;
+    }
     case IBM_LBM_STAGE_COLLIDE:
-      launch_collide(h->L, h->cfg.storage, h->odd_next, true, st);
+      launch_collide(lat(h, h->odd_next), h->rows, h->n_rows, h->cfg.storage, h->odd_next, true, st);
       h->odd_next = !h->odd_next;
       break;
     case IBM_LBM_STAGE_INTERP:
-      launch_interpolate(h->L, h->m, st);
+      launch_interpolate(h->L, h->m, h->groups, h->n_groups, h->boxes, st);
       h->steps += 1;
       break;
     default:
@@ -660,7 +842,7 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
   const size_t N = (size_t)h->L.N;
   std::vector<float4> tmp(N);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpy(tmp.data(), h->L.g, sizeof(float4) * N, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(tmp.data(), h->gbuf[h->odd_next ? 1 : 0], sizeof(float4) * N, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < N; ++i) {
     g[i] = tmp[i].x; g[N + i] = tmp[i].y; g[2 * N + i] = tmp[i].z;
   }
@@ -739,6 +921,7 @@ int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   for (auto e : h->events) cudaEventDestroy(e);
   h->events.clear();
   h->timed_steps = 0;
+  h->timed_odd.clear();
   h->timing = max_steps > 0;
   for (int64_t i = 0; i < 5 * max_steps; ++i) {
     cudaEvent_t e;
@@ -748,18 +931,20 @@ int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_timing(ibm_lbm_t* h, double out[5]) {
+int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
   if (!h || !out) return IBM_LBM_E_ARG;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  for (int k = 0; k < 6; ++k) out[k] = 0.0;
   for (size_t s = 0; s < h->timed_steps; ++s)
     for (int k = 0; k < 4; ++k) {
       float ms = 0.f;
       CUDA_TRY(h, cudaEventElapsedTime(&ms, h->events[5 * s + k], h->events[5 * s + k + 1]));
       out[k] += ms;
+      if (k == 2 && h->timed_odd[s]) out[5] += ms;
     }
   out[4] = (double)h->timed_steps;
   h->timed_steps = 0;
+  h->timed_odd.clear();
   return IBM_LBM_OK;
 }
 

@@ -54,9 +54,33 @@ struct LatticeDev {
   int ntx, nty, ntz;     // tile grid
   void* pop;             // [19][N] in the storage type
   float4* uw;            // moments of the last collision: (ux, uy, uz, rho - 1) [N]
-  float4* g;             // spread force density (gx, gy, gz, 0) [N], zeroed by the collision
+  // Force density and touched-tile flags are double-buffered by step parity:
+  // this step spreads into g / flags and the collision reads them; the
+  // collision also clears g_next where flags_next (the previous step's tiles)
+  // is set, so that buffer starts the next step at zero. Reading and clearing
+  // the same words in one pass is avoided on purpose.
+  float4* g;             // spread force density (gx, gy, gz, 0) [N]
   uint8_t* flags;        // [ntx*nty*ntz]: tile touched by a marker stencil this step
+  float4* g_next;        // the other buffer, cleared where flags_next is set
+  const uint8_t* flags_next;
   int* status;           // device status word (0 = OK)
+};
+
+// One lattice row (fixed y, z; all x) that holds fluid. Solidity depends on
+// (y, z) only in every geometry, so a row is all fluid or all solid and the
+// collide kernel runs over the fluid rows alone.
+struct RowInfo {
+  int base;              // idx of (0, y, z)
+  int smask;             // bit (dy+1)*3 + (dz+1): the row at (y+dy, z+dz) is solid
+  int oyp, oym, ozp, ozm;// wrapped element offsets to the y+-1, z+-1 rows
+  int y;
+  int trow;              // tile-row offset ntx * ((y >> 2) + nty * (z >> 2))
+};
+
+// A contiguous run of markers handled by one thread block in the transfer
+// kernels (a body, or part of one, or a run of passive tracers).
+struct MarkerGroup {
+  int first, count;
 };
 
 // Solid test of a node with wrapped x and (for walls/tube) raw y, z.
@@ -112,10 +136,16 @@ struct BodyDev {
 
 struct MeshDev {
   int nv, nt, ne;
-  const int4* edges;      // (a, b, c, d): edge a->b, wing c in the triangle with a->b, d in the other
-  const float2* edge_rest;// (l0, theta0)
-  const int4* tris;       // (v0, v1, v2, -)
-  const float* tri_area0; // A_t0
+  // Template topology packed in one buffer of 16-byte-aligned sections:
+  // edges ushort4 (a, b, c, d): edge a->b, wing c in the triangle with a->b,
+  // d in the other; edge_tris ushort2 (t1, t2): those two triangles;
+  // edge_rest float2 (l0, theta0); tris ushort4 (v0, v1, v2, -); area0 float;
+  // per-vertex CSR lists ve_start/ve of (edge << 2 | role a,b,c,d) and
+  // vt_start/vt of (triangle << 2 | slot), all unsigned short.
+  const unsigned char* packed;
+  int packed_bytes;  // multiple of 16
+  int off_edges, off_edge_tris, off_edge_rest, off_tris, off_area0, off_ve_start, off_ve, off_vt_start, off_vt;
+  int work_floats;   // per-body shared work area: 6 nv + 4 nt + 2 ne floats
   float A0, V0;
 };
 

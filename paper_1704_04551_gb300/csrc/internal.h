@@ -7,20 +7,25 @@
 namespace ibm {
 
 // lbm.cu
-void launch_collide(const LatticeDev& L, int storage, bool odd, bool dense, cudaStream_t st);
+void launch_collide(const LatticeDev& L, const RowInfo* rows, int n_rows, int storage, bool odd, bool dense,
+                    cudaStream_t st);
 void launch_init_equilibrium(const LatticeDev& L, int storage, cudaStream_t st);
 void launch_export(const LatticeDev& L, int storage, bool odd_next, double* out, cudaStream_t st);
 void launch_import(const LatticeDev& L, int storage, const double* in, cudaStream_t st);
-void launch_diagnostics(const LatticeDev& L, double* out, unsigned* umax2_bits, cudaStream_t st);
+void launch_diagnostics(const LatticeDev& L, const RowInfo* rows, int n_rows, double* out, unsigned* umax2_bits,
+                        cudaStream_t st);
 
 // transfer.cu
-void launch_spread(const LatticeDev& L, const MarkersDev& m, cudaStream_t st);
-void launch_interpolate(const LatticeDev& L, const MarkersDev& m, cudaStream_t st);
+void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups, int4* boxes,
+                   cudaStream_t st);
+void launch_interpolate(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups,
+                        const int4* boxes, cudaStream_t st);
+cudaError_t transfer_configure();
 
 // forces.cu
-void launch_forces(const MarkersDev& m, BodyDev* bodies, int n_bodies, const MeshDev& mesh,
-                   cudaStream_t st);
-size_t forces_smem_bytes(int nv);
-cudaError_t forces_configure(size_t smem_bytes);
+void launch_forces(const MarkersDev& m, BodyDev* bodies, const int* membranes, int n_membranes, const int* rigids,
+                   int n_rigids, const MeshDev& mesh, bool persistent, int n_sm, cudaStream_t st);
+size_t membrane_work_floats(int nv, int nt, int ne);
+cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem, bool* persistent);
 
 }  // namespace ibm

@@ -85,27 +85,46 @@ __device__ __forceinline__ bool nb_solid(const Cell& c, int i, int s) {
 
 }  // namespace
 
-// Fused collide-stream-force kernel, one thread per cell.
+// Fused collide-stream-force kernel: one thread per fluid cell, a 2-D grid
+// over (x, fluid row). Row data (offsets of the neighbouring rows, which of
+// them are solid) come from the precomputed row table, so a thread does no
+// integer division and no geometry arithmetic.
+constexpr int COLLIDE_THREADS = 128;
+#ifndef IBM_COLLIDE_MIN_BLOCKS
+#define IBM_COLLIDE_MIN_BLOCKS 8  // resident blocks per SM the register budget is sized for
+#endif
+
 template <int S, int ODD, int GEOM, bool DENSE>
-__global__ void __launch_bounds__(256) k_collide(LatticeDev L) {
+__global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
+                                                                int n_rows) {
   using P = Pop<S>;
   using T = typename P::T;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L.N) return;
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows || x >= L.nx) return;
+  const RowInfo R = rows[r];
+  const int idx = R.base + x;
   Cell c;
-  if (!make_cell<GEOM>(L, idx, c)) return;
+  c.x = x;
+  c.y = R.y;
+  c.smask = (unsigned)R.smask;
+  c.oxp = (x == L.nx - 1) ? 1 - L.nx : 1;
+  c.oxm = (x == 0) ? L.nx - 1 : -1;
+  c.oyp = R.oyp; c.oym = R.oym; c.ozp = R.ozp; c.ozm = R.ozm;
   T* A = reinterpret_cast<T*>(L.pop);
   const size_t N = (size_t)L.N;
 
+  // f_j(x) sits at A[x][j] (even step) or at A[x - c_j][opp(j)] (odd step;
+  // A[x][j] if x - c_j is solid). In both parities f*_i(x) goes back to the
+  // slot that held f_opp(i)(x), which covers streaming and half-way
+  // bounce-back alike.
   float d[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (!ODD || i == 0) {
-      d[i] = P::ld(A + i * N + idx, i);
-    } else {
-      const bool sol = (GEOM != GEOM_PERIODIC) && nb_solid(c, i, -1);
-      d[i] = sol ? P::ld(A + i * N + idx, i) : P::ld(A + opp(i) * N + (idx + nb_off(c, i, -1)), opp(i));
-    }
+  for (int j = 0; j < Q; ++j) {
+    if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1)))
+      d[j] = P::ld(A + (size_t)j * N + idx, j);
+    else
+      d[j] = P::ld(A + (size_t)opp(j) * N + (idx + nb_off(c, j, -1)), opp(j));
   }
 
   // moments (Eq. rho_u): rho = sum f, rho u = sum f c + g/2
@@ -118,13 +137,13 @@ __global__ void __launch_bounds__(256) k_collide(LatticeDev L) {
     if (cz(i)) jz += cz(i) * d[i];
   }
   float Gx = L.g0x, Gy = L.g0y, Gz = L.g0z;
-  const int tile = (c.x >> TILE_X_SHIFT) + L.ntx * ((c.y >> TILE_Y_SHIFT) + L.nty * (c.z >> TILE_Z_SHIFT));
+  const int tile = R.trow + (x >> TILE_X_SHIFT);
   const bool touched = L.flags[tile] != 0;
   if (touched) {
     const float4 gg = L.g[idx];
     Gx += gg.x; Gy += gg.y; Gz += gg.z;
-    L.g[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  if (L.flags_next[tile]) L.g_next[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
   const float rho = 1.0f + drho;
   const float irho = 1.0f / rho;
   const float ux = (jx + 0.5f * Gx) * irho;
@@ -146,23 +165,24 @@ __global__ void __launch_bounds__(256) k_collide(LatticeDev L) {
     d[i] = d[i] + om * (deq - d[i]) + Fi;
   }
 
+  // Recompute the write addresses from a few laundered registers instead of
+  // keeping the 19 read addresses alive across the collision (which spills).
+  int widx = idx;
+  asm volatile("" : "+r"(widx), "+r"(c.oxp), "+r"(c.oxm), "+r"(c.oyp), "+r"(c.oym), "+r"(c.ozp), "+r"(c.ozm),
+               "+r"(c.smask));
   // streaming with half-way bounce-back (moving-wall term on y walls)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     float v = d[i];
-    bool sol = false;
-    if (GEOM != GEOM_PERIODIC && i != 0) {
-      sol = nb_solid(c, i, +1);
-      if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
-        const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
-        v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
-      }
+    const bool sol = (GEOM != GEOM_PERIODIC) && i != 0 && nb_solid(c, i, +1);
+    if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
+      const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
+      v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
     }
-    if (!ODD || i == 0 || sol) {
-      P::st(A + opp(i) * N + idx, opp(i), v);
-    } else {
-      P::st(A + i * N + (idx + nb_off(c, i, +1)), i, v);
-    }
+    if (!ODD || i == 0 || sol)
+      P::st(A + (size_t)opp(i) * N + widx, opp(i), v);
+    else
+      P::st(A + (size_t)i * N + (widx + nb_off(c, i, +1)), i, v);
   }
 }
 
@@ -236,23 +256,22 @@ __global__ void k_import(LatticeDev L, const double* in) {
 // the finiteness check. out: [0] sum(rho - 1), [1..3] sum rho u, [4] number
 // of fluid cells; *umax2_bits: max |u|^2 as float bits (atomicMax on the
 // bits orders non-negative floats).
-template <int GEOM>
-__global__ void __launch_bounds__(256) k_diagnostics(LatticeDev L, double* out, unsigned* umax2_bits) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_diagnostics(LatticeDev L, const RowInfo* __restrict__ rows, int n_rows,
+                                                     double* out, unsigned* umax2_bits) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
   float m2 = 0.f;
   bool bad = false;
-  if (idx < L.N) {
-    Cell c;
-    if (make_cell<GEOM>(L, idx, c)) {
-      const float4 m = L.uw[idx];
-      const double rho = 1.0 + (double)m.w;
-      s0 = (double)m.w;
-      s1 = rho * m.x; s2 = rho * m.y; s3 = rho * m.z;
-      s4 = 1.0;
-      m2 = m.x * m.x + m.y * m.y + m.z * m.z;
-      bad = !(isfinite(m.x) && isfinite(m.y) && isfinite(m.z) && isfinite(m.w));
-    }
+  const long long n = (long long)n_rows * L.nx;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / L.nx);
+    const int idx = rows[r].base + (int)(t - (long long)r * L.nx);
+    const float4 m = L.uw[idx];
+    const double rho = 1.0 + (double)m.w;
+    s0 += (double)m.w;
+    s1 += rho * m.x; s2 += rho * m.y; s3 += rho * m.z;
+    s4 += 1.0;
+    m2 = fmaxf(m2, m.x * m.x + m.y * m.y + m.z * m.z);
+    bad = bad || !(isfinite(m.x) && isfinite(m.y) && isfinite(m.z) && isfinite(m.w));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -304,22 +323,24 @@ namespace {
 inline unsigned blocks_for(int n) { return (unsigned)((n + 255) / 256); }
 
 template <int S, int GEOM>
-void launch_collide_g(const LatticeDev& L, bool odd, bool dense, cudaStream_t st) {
-  const unsigned nb = blocks_for(L.N);
+void launch_collide_g(const LatticeDev& L, const RowInfo* rows, int n_rows, bool odd, bool dense, cudaStream_t st) {
+  const int tx = L.nx >= COLLIDE_THREADS ? COLLIDE_THREADS : ((L.nx + 31) / 32) * 32;
+  const int ty = COLLIDE_THREADS / tx;
+  const dim3 block(tx, ty), grid((L.nx + tx - 1) / tx, (n_rows + ty - 1) / ty);
   if (odd) {
-    if (dense) k_collide<S, 1, GEOM, true><<<nb, 256, 0, st>>>(L);
-    else k_collide<S, 1, GEOM, false><<<nb, 256, 0, st>>>(L);
+    if (dense) k_collide<S, 1, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows);
+    else k_collide<S, 1, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows);
   } else {
-    if (dense) k_collide<S, 0, GEOM, true><<<nb, 256, 0, st>>>(L);
-    else k_collide<S, 0, GEOM, false><<<nb, 256, 0, st>>>(L);
+    if (dense) k_collide<S, 0, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows);
+    else k_collide<S, 0, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows);
   }
 }
 template <int S>
-void launch_collide_s(const LatticeDev& L, bool odd, bool dense, cudaStream_t st) {
+void launch_collide_s(const LatticeDev& L, const RowInfo* rows, int n_rows, bool odd, bool dense, cudaStream_t st) {
   switch (L.geometry) {
-    case GEOM_PERIODIC: launch_collide_g<S, GEOM_PERIODIC>(L, odd, dense, st); break;
-    case GEOM_YWALLS: launch_collide_g<S, GEOM_YWALLS>(L, odd, dense, st); break;
-    default: launch_collide_g<S, GEOM_TUBE>(L, odd, dense, st); break;
+    case GEOM_PERIODIC: launch_collide_g<S, GEOM_PERIODIC>(L, rows, n_rows, odd, dense, st); break;
+    case GEOM_YWALLS: launch_collide_g<S, GEOM_YWALLS>(L, rows, n_rows, odd, dense, st); break;
+    default: launch_collide_g<S, GEOM_TUBE>(L, rows, n_rows, odd, dense, st); break;
   }
 }
 template <int S, int GEOM>
@@ -349,11 +370,13 @@ void launch_export_s(const LatticeDev& L, bool odd_next, double* out, cudaStream
 }
 }  // namespace
 
-void launch_collide(const LatticeDev& L, int storage, bool odd, bool dense, cudaStream_t st) {
+void launch_collide(const LatticeDev& L, const RowInfo* rows, int n_rows, int storage, bool odd, bool dense,
+                    cudaStream_t st) {
+  if (n_rows == 0) return;
   switch (storage) {
-    case STORE_F32: launch_collide_s<STORE_F32>(L, odd, dense, st); break;
-    case STORE_F16: launch_collide_s<STORE_F16>(L, odd, dense, st); break;
-    default: launch_collide_s<STORE_BF16>(L, odd, dense, st); break;
+    case STORE_F32: launch_collide_s<STORE_F32>(L, rows, n_rows, odd, dense, st); break;
+    case STORE_F16: launch_collide_s<STORE_F16>(L, rows, n_rows, odd, dense, st); break;
+    default: launch_collide_s<STORE_BF16>(L, rows, n_rows, odd, dense, st); break;
   }
 }
 
@@ -381,12 +404,12 @@ void launch_import(const LatticeDev& L, int storage, const double* in, cudaStrea
   }
 }
 
-void launch_diagnostics(const LatticeDev& L, double* out, unsigned* umax2_bits, cudaStream_t st) {
-  switch (L.geometry) {
-    case GEOM_PERIODIC: k_diagnostics<GEOM_PERIODIC><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
-    case GEOM_YWALLS: k_diagnostics<GEOM_YWALLS><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
-    default: k_diagnostics<GEOM_TUBE><<<blocks_for(L.N), 256, 0, st>>>(L, out, umax2_bits); break;
-  }
+void launch_diagnostics(const LatticeDev& L, const RowInfo* rows, int n_rows, double* out, unsigned* umax2_bits,
+                        cudaStream_t st) {
+  const long long n = (long long)n_rows * L.nx;
+  if (n == 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_diagnostics<<<(unsigned)(blocks < 1216 ? blocks : 1216), 256, 0, st>>>(L, rows, n_rows, out, umax2_bits);
 }
 
 }  // namespace ibm

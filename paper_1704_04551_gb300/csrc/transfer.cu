@@ -6,12 +6,33 @@
 // |r| <= 2 (Eq. deltaPhiSimple). The 4-point stencil of a marker at X is the
 // nodes floor(X)-1 .. floor(X)+2 on each axis; nodes inside walls or the
 // tube's solid are skipped (no renormalisation). Periodic axes wrap.
+//
+// One thread block per marker group (a body, or a run of tracers), four
+// threads per marker (one per x offset of the stencil, so the four read or
+// write consecutive words). The block bounds the group's stencils with a
+// box; when the box fits in shared memory (BOX_CELLS cells):
+//   spreading accumulates there in 32-bit fixed point (native integer
+//   shared-memory atomics; the sum does not depend on the order of the
+//   additions) with a scale chosen from the group's largest force so that no
+//   cell can overflow, then adds the box's nonzero cells to global memory
+//   (one float4 atomic each);
+//   interpolation loads the box of velocities once and gathers from shared
+//   memory.
+// Larger boxes (scattered tracers, very large bodies) fall back to
+// per-marker global float4 atomics / gathers. The box of each group is
+// computed by the spread kernel and reused by the interpolation of the same
+// step (markers do not move in between).
+#include <climits>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace ibm {
 
 namespace {
+
+constexpr int XFER_THREADS = 512;   // two blocks per SM (shared-memory box), 32 warps
+constexpr int BOX_CELLS = 8192;  // 3 floats per cell: 96 KiB of shared memory
 
 struct Stencil {
   int bx, by, bz;        // first node on each axis (unwrapped)
@@ -33,100 +54,282 @@ __device__ __forceinline__ void make_stencil(double X, double Y, double Z, Stenc
   }
 }
 
+// wrap / range handling of a stencil row (y, z) for the geometry; false if
+// the row is solid (outside the walls or the tube, or out of range)
+template <int GEOM>
+__device__ __forceinline__ bool fluid_row(const LatticeDev& L, int& y, int& z) {
+  if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
+  if (GEOM == GEOM_PERIODIC) {
+    y = wrapi(y, L.ny);
+    return true;
+  }
+  return !solid_yz(L, y, z);
+}
+
+// Mark the (at most 8) tiles covered by a marker's stencil.
+template <int GEOM>
+__device__ __forceinline__ void mark_tiles(const LatticeDev& L, const Stencil& s) {
+  int tx[2], ty[2], tz[2], nxt = 0, nyt = 0, nzt = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int t = wrapi(s.bx + a, L.nx) >> TILE_X_SHIFT;
+    if (nxt == 0 || tx[nxt - 1] != t) { if (nxt < 2) tx[nxt++] = t; }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int y = s.by + a;
+    if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
+    else if ((unsigned)y >= (unsigned)L.ny) continue;
+    const int t = y >> TILE_Y_SHIFT;
+    if (nyt == 0 || ty[nyt - 1] != t) { if (nyt < 2) ty[nyt++] = t; }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int z = s.bz + a;
+    if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
+    else if ((unsigned)z >= (unsigned)L.nz) continue;
+    const int t = z >> TILE_Z_SHIFT;
+    if (nzt == 0 || tz[nzt - 1] != t) { if (nzt < 2) tz[nzt++] = t; }
+  }
+  for (int c = 0; c < nzt; ++c)
+    for (int b = 0; b < nyt; ++b)
+      for (int a = 0; a < nxt; ++a) L.flags[tx[a] + L.ntx * (ty[b] + L.nty * tz[c])] = 1;
+}
+
+// Bounding box of the group's stencil nodes (unwrapped coordinates):
+// lo = min floor(X) - 1, dims = max floor(X) - min floor(X) + 4.
+__device__ void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, int4& dims) {
+  __shared__ int s_lo[3], s_hi[3];
+  if (threadIdx.x < 3) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  __syncthreads();
+  const size_t M = (size_t)m.M;
+  int lx = INT_MAX, ly = INT_MAX, lz = INT_MAX, hx = INT_MIN, hy = INT_MIN, hz = INT_MIN;
+  for (int k = G.first + threadIdx.x; k < G.first + G.count; k += blockDim.x) {
+    const int fx = (int)floor(m.X[k]), fy = (int)floor(m.X[M + k]), fz = (int)floor(m.X[2 * M + k]);
+    lx = min(lx, fx); ly = min(ly, fy); lz = min(lz, fz);
+    hx = max(hx, fx); hy = max(hy, fy); hz = max(hz, fz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = min(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+    ly = min(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+    lz = min(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+    hx = max(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+    hy = max(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+    hz = max(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&s_lo[0], lx); atomicMin(&s_lo[1], ly); atomicMin(&s_lo[2], lz);
+    atomicMax(&s_hi[0], hx); atomicMax(&s_hi[1], hy); atomicMax(&s_hi[2], hz);
+  }
+  __syncthreads();
+  const long long ex = (long long)s_hi[0] - s_lo[0] + 4, ey = (long long)s_hi[1] - s_lo[1] + 4,
+                  ez = (long long)s_hi[2] - s_lo[2] + 4;
+  lo = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, 0);
+  const bool fits = ex > 0 && ey > 0 && ez > 0 && ex * ey * ez <= BOX_CELLS;
+  dims = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
+}
+
 }  // namespace
 
 template <int GEOM>
-__global__ void __launch_bounds__(256) k_spread(LatticeDev L, MarkersDev m) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m.M) return;
+__global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, MarkersDev m, const MarkerGroup* groups,
+                                                         int4* boxes) {
+  extern __shared__ __align__(16) int ibox[];  // [3][vol] fixed-point sums
+  __shared__ unsigned s_fmax_bits;
+  const MarkerGroup G = groups[blockIdx.x];
+  int4 lo, dims;
+  if (threadIdx.x == 0) s_fmax_bits = 0u;
+  group_box(m, G, lo, dims);  // synchronises
+  if (threadIdx.x == 0) {
+    boxes[2 * blockIdx.x] = lo;
+    boxes[2 * blockIdx.x + 1] = dims;
+  }
   const size_t M = (size_t)m.M;
-  Stencil s;
-  make_stencil(m.X[k], m.X[M + k], m.X[2 * M + k], s);
-  const float4 F = m.F[k];
-  int xs[4], tx[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    xs[a] = wrapi(s.bx + a, L.nx);
-    tx[a] = xs[a] >> TILE_X_SHIFT;
+  // largest force component of the group (non-negative floats order as their bits)
+  float fm = 0.f;
+  for (int k = G.first + threadIdx.x; k < G.first + G.count; k += blockDim.x) {
+    const float4 F = m.F[k];
+    fm = fmaxf(fm, fmaxf(fabsf(F.x), fmaxf(fabsf(F.y), fabsf(F.z))));
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    int z = s.bz + c;
-    if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
+  for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_fmax_bits, __float_as_uint(fm));
+  __syncthreads();
+  const float fmax = __uint_as_float(s_fmax_bits);
+  const bool any_force = fmax > 0.f;
+  const bool in_smem = dims.w != 0;
+  const int vol = dims.x * dims.y * dims.z;
+  // |sum| in any cell <= count * fmax / 8 (delta <= 1/8); map that bound to 2^30
+  const float bound = fmax * (float)G.count * 0.125f;
+  const float S = any_force ? fminf(1073741824.0f / bound, 1e30f) : 0.f;
+  if (in_smem && any_force) {
+    for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
+    __syncthreads();
+  }
+  const int a = threadIdx.x & 3;
+  for (int j = threadIdx.x >> 2; j < G.count; j += blockDim.x >> 2) {
+    const int k = G.first + j;
+    Stencil s;
+    make_stencil(m.X[k], m.X[M + k], m.X[2 * M + k], s);
+    if (a == 0) mark_tiles<GEOM>(L, s);
+    if (!any_force) continue;
+    const float4 F = m.F[k];
+    if (in_smem) {
+      const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int y = s.by + b;
-      if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
-      if (GEOM != GEOM_PERIODIC && solid_yz(L, y, z)) continue;
-      const float wyz = s.wy[b] * s.wz[c];
-      const int row = L.nx * (y + L.ny * z);
-      const int trow = L.ntx * ((y >> TILE_Y_SHIFT) + L.nty * (z >> TILE_Z_SHIFT));
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float w = s.wx[a] * wyz;
-        atomicAdd(L.g + row + xs[a], make_float4(F.x * w, F.y * w, F.z * w, 0.f));
-        if (a == 0 || tx[a] != tx[a - 1]) L.flags[trow + tx[a]] = 1;
+        for (int b = 0; b < 4; ++b) {
+          const float w = s.wx[a] * s.wy[b] * s.wz[c] * S;
+          const int li = li0 + dims.x * (b + dims.y * c);
+          atomicAdd(ibox + li, __float2int_rn(F.x * w));
+          atomicAdd(ibox + vol + li, __float2int_rn(F.y * w));
+          atomicAdd(ibox + 2 * vol + li, __float2int_rn(F.z * w));
+        }
+    } else {
+      const int x = wrapi(s.bx + a, L.nx);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int y = s.by + b, z = s.bz + c;
+          if (!fluid_row<GEOM>(L, y, z)) continue;
+          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          atomicAdd(L.g + L.nx * (y + L.ny * z) + x, make_float4(F.x * w, F.y * w, F.z * w, 0.f));
+        }
       }
     }
+  }
+  if (!in_smem || !any_force) return;
+  __syncthreads();
+  // add the nonzero cells of the box to the lattice
+  const float inv = 1.0f / S;
+  for (int li = threadIdx.x; li < vol; li += blockDim.x) {
+    const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
+    if ((qx | qy | qz) == 0) continue;
+    const int ax = li % dims.x, t = li / dims.x, ay = t % dims.y, az = t / dims.y;
+    int y = lo.y + ay, z = lo.z + az;
+    if (!fluid_row<GEOM>(L, y, z)) continue;
+    atomicAdd(L.g + L.nx * (y + L.ny * z) + wrapi(lo.x + ax, L.nx),
+              make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
   }
 }
 
 template <int GEOM>
-__global__ void __launch_bounds__(256) k_interpolate(LatticeDev L, MarkersDev m) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m.M) return;
+__global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, MarkersDev m, const MarkerGroup* groups,
+                                                              const int4* boxes) {
+  extern __shared__ __align__(16) float box[];  // [3][vol]
+  const MarkerGroup G = groups[blockIdx.x];
+  const int4 lo = boxes[2 * blockIdx.x], dims = boxes[2 * blockIdx.x + 1];
   const size_t M = (size_t)m.M;
-  const double X = m.X[k], Y = m.X[M + k], Z = m.X[2 * M + k];
-  Stencil s;
-  make_stencil(X, Y, Z, s);
-  int xs[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) xs[a] = wrapi(s.bx + a, L.nx);
-  float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    int z = s.bz + c;
-    if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int y = s.by + b;
-      if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
-      if (GEOM != GEOM_PERIODIC && solid_yz(L, y, z)) continue;
-      const float wyz = s.wy[b] * s.wz[c];
+  const bool in_smem = dims.w != 0;
+  const int vol = dims.x * dims.y * dims.z;
+  if (in_smem) {
+    // load the box of velocities row by row; solid rows contribute zero
+    const int nrows = dims.y * dims.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int r = warp; r < nrows; r += nwarps) {
+      int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
+      const bool fl = fluid_row<GEOM>(L, y, z);
       const float4* row = L.uw + L.nx * (y + L.ny * z);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float w = s.wx[a] * wyz;
-        const float4 u = row[xs[a]];
-        ux = fmaf(w, u.x, ux);
-        uy = fmaf(w, u.y, uy);
-        uz = fmaf(w, u.z, uz);
+      for (int ax = lane; ax < dims.x; ax += 32) {
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fl) u = row[wrapi(lo.x + ax, L.nx)];
+        const int li = r * dims.x + ax;
+        box[li] = u.x;
+        box[vol + li] = u.y;
+        box[2 * vol + li] = u.z;
       }
     }
+    __syncthreads();
   }
-  m.U[k] = make_float4(ux, uy, uz, 0.f);
-  m.X[k] = X + (double)ux;
-  m.X[M + k] = Y + (double)uy;
-  m.X[2 * M + k] = Z + (double)uz;
+  const int a = threadIdx.x & 3;
+  // every thread of a 4-lane group runs the same iterations (shuffles below)
+  for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
+    const int j = j0 + (threadIdx.x >> 2);
+    const bool active = j < G.count;
+    const int k = G.first + (active ? j : 0);
+    const double X = m.X[k], Y = m.X[M + k], Z = m.X[2 * M + k];
+    Stencil s;
+    make_stencil(X, Y, Z, s);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (in_smem) {
+      const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          const int li = li0 + dims.x * (b + dims.y * c);
+          ux = fmaf(w, box[li], ux);
+          uy = fmaf(w, box[vol + li], uy);
+          uz = fmaf(w, box[2 * vol + li], uz);
+        }
+    } else {
+      const int x = wrapi(s.bx + a, L.nx);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int y = s.by + b, z = s.bz + c;
+          if (!fluid_row<GEOM>(L, y, z)) continue;
+          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          const float4 u = L.uw[L.nx * (y + L.ny * z) + x];
+          ux = fmaf(w, u.x, ux);
+          uy = fmaf(w, u.y, uy);
+          uz = fmaf(w, u.z, uz);
+        }
+      }
+    }
+    // sum the four x columns of the stencil
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      ux += __shfl_xor_sync(0xffffffffu, ux, o);
+      uy += __shfl_xor_sync(0xffffffffu, uy, o);
+      uz += __shfl_xor_sync(0xffffffffu, uz, o);
+    }
+    if (active && a == 0) {
+      m.U[k] = make_float4(ux, uy, uz, 0.f);
+      m.X[k] = X + (double)ux;
+      m.X[M + k] = Y + (double)uy;
+      m.X[2 * M + k] = Z + (double)uz;
+    }
+  }
 }
 
-void launch_spread(const LatticeDev& L, const MarkersDev& m, cudaStream_t st) {
-  if (m.M == 0) return;
-  const unsigned nb = (unsigned)((m.M + 255) / 256);
+cudaError_t transfer_configure() {
+  cudaError_t e = cudaSuccess;
+  const int smem = 3 * BOX_CELLS * (int)sizeof(float);
+#define CFG(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+  CFG(k_spread<GEOM_PERIODIC>); CFG(k_spread<GEOM_YWALLS>); CFG(k_spread<GEOM_TUBE>);
+  CFG(k_interpolate<GEOM_PERIODIC>); CFG(k_interpolate<GEOM_YWALLS>); CFG(k_interpolate<GEOM_TUBE>);
+#undef CFG
+  return e;
+}
+
+void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups, int4* boxes,
+                   cudaStream_t st) {
+  if (m.M == 0 || n_groups == 0) return;
+  const size_t smem = 3 * BOX_CELLS * sizeof(float);
   switch (L.geometry) {
-    case GEOM_PERIODIC: k_spread<GEOM_PERIODIC><<<nb, 256, 0, st>>>(L, m); break;
-    case GEOM_YWALLS: k_spread<GEOM_YWALLS><<<nb, 256, 0, st>>>(L, m); break;
-    default: k_spread<GEOM_TUBE><<<nb, 256, 0, st>>>(L, m); break;
+    case GEOM_PERIODIC: k_spread<GEOM_PERIODIC><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
+    case GEOM_YWALLS: k_spread<GEOM_YWALLS><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
+    default: k_spread<GEOM_TUBE><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
   }
 }
 
-void launch_interpolate(const LatticeDev& L, const MarkersDev& m, cudaStream_t st) {
-  if (m.M == 0) return;
-  const unsigned nb = (unsigned)((m.M + 255) / 256);
+void launch_interpolate(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups,
+                        const int4* boxes, cudaStream_t st) {
+  if (m.M == 0 || n_groups == 0) return;
+  const size_t smem = 3 * BOX_CELLS * sizeof(float);
   switch (L.geometry) {
-    case GEOM_PERIODIC: k_interpolate<GEOM_PERIODIC><<<nb, 256, 0, st>>>(L, m); break;
-    case GEOM_YWALLS: k_interpolate<GEOM_YWALLS><<<nb, 256, 0, st>>>(L, m); break;
-    default: k_interpolate<GEOM_TUBE><<<nb, 256, 0, st>>>(L, m); break;
+    case GEOM_PERIODIC: k_interpolate<GEOM_PERIODIC><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
+    case GEOM_YWALLS: k_interpolate<GEOM_YWALLS><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
+    default: k_interpolate<GEOM_TUBE><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
   }
 }
 
