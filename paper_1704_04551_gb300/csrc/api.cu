@@ -53,7 +53,6 @@ struct ibm_lbm {
   int* membrane_list = nullptr;   // body indices of membranes / rigid bodies
   int* rigid_list = nullptr;
   int n_membranes = 0, n_rigids = 0;
-  bool persistent_forces = false;
   int n_sm = 0;
   MarkerGroup* groups = nullptr;  // transfer blocks
   int n_groups = 0;
@@ -148,8 +147,7 @@ void enqueue_step(ibm_lbm_t* h, bool odd, bool dense) {
   cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
   if (h->m.M > 0) {
     if (h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
-    launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
-                  h->persistent_forces, h->n_sm, st);
+    launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
     launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   }
   launch_collide(L, h->rows, h->n_rows, h->cfg.storage, odd, dense, st);
@@ -168,8 +166,7 @@ void enqueue_timed_step(ibm_lbm_t* h, bool odd, bool dense) {
   cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
   if (h->m.M > 0 && h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
   mark(0);
-  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
-                  h->persistent_forces, h->n_sm, st);
+  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
   mark(1);
   if (h->m.M > 0) launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   mark(2);
@@ -616,7 +613,6 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   h->mesh = MeshDev{};
   h->membrane_list = h->rigid_list = nullptr;
   h->n_membranes = h->n_rigids = 0;
-  h->persistent_forces = false;
   h->groups = nullptr;
   h->n_groups = 0;
   h->boxes = nullptr;
@@ -660,7 +656,12 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   if ((rc = upload<double>(h, h->marker_mem, &h->m.X, X, 3 * (size_t)M))) return rc;
   h->m.U = (float4*)dalloc(h, h->marker_mem, sizeof(float4) * (size_t)M);
   h->m.F = (float4*)dalloc(h, h->marker_mem, sizeof(float4) * (size_t)M);
-  if (!h->m.U || !h->m.F) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  h->m.cell = (int*)dalloc(h, h->marker_mem, sizeof(int) * 3 * (size_t)M);
+  h->m.frac = (float*)dalloc(h, h->marker_mem, sizeof(float) * 3 * (size_t)M);
+  if (!h->m.U || !h->m.F || !h->m.cell || !h->m.frac) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  launch_stencil_cache(h->m, h->stream);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaMemset(h->m.U, 0, sizeof(float4) * (size_t)std::max(M, 1)));
   CUDA_TRY(h, cudaMemset(h->m.F, 0, sizeof(float4) * (size_t)std::max(M, 1)));
   // rigid body-frame offsets r_k = R^T (X_k - C)
@@ -749,7 +750,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     int dev = 0, optin = 0;
     CUDA_TRY(h, cudaGetDevice(&dev));
     CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (forces_configure(D, (size_t)optin, &h->persistent_forces) != cudaSuccess) {
+    if (forces_configure(D, (size_t)optin) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, IBM_LBM_E_ARG, "set_markers: membrane template too large for one thread block's shared memory");
     }
@@ -801,8 +802,7 @@ int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
     case IBM_LBM_STAGE_FORCES:
       if (h->m.M > 0) {
         if (h->need_zero_F) CUDA_TRY(h, cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st));
-        launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh,
-                  h->persistent_forces, h->n_sm, st);
+        launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
       }
       break;
     case IBM_LBM_STAGE_SPREAD: {

@@ -151,10 +151,16 @@ struct MeshDev {
 
 struct MarkersDev {
   int M;
-  double* X;          // [3][M]
+  double* X;          // [3][M] positions (FP64, unwrapped)
   float4* U;          // (Ux, Uy, Uz, 0) [M]
   float4* F;          // (Fx, Fy, Fz, 0) [M]
   const double* ref;  // rigid body-frame offsets [3][M]
+  // Stencil cache of the current positions: cell[a][k] = floor(X_a,k) and
+  // frac[a][k] = X_a,k - floor(X_a,k) rounded once to FP32. Written when the
+  // positions change (set_markers, advection) so that the force, spreading
+  // and interpolation kernels need no FP64 arithmetic.
+  int* cell;          // [3][M]
+  float* frac;        // [3][M]
 };
 
 }  // namespace ibm

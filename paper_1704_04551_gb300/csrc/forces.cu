@@ -10,22 +10,22 @@
 //               triangles sharing the edge (positive where convex);
 //   U_area    = k_g (A - A0)^2 / (2 A0) + sum_t k_l (A_t - A_t0)^2/(2 A_t0) (Eq. areaEnergy)
 //   U_volume  = k_v (V - V0)^2 / (2 V0)                                    (Eq. volumeEnergy)
-// Positions are FP64. Each vertex is loaded once as its offset from the
-// body's first vertex, split into an FP32 pair (hi, lo) with hi + lo equal to
-// the FP64 offset to ~2^-48 relative; the difference of two vertices is
-// (hi_a - hi_b) + (lo_a - lo_b), accurate to FP32 rounding of the difference
-// itself, with no FP64 arithmetic (slow on this GPU). All force arithmetic is
-// FP32; the body's total area and volume are reduced in FP64. The volume
-// gradient at a vertex uses the closed-surface form
-// dV/dx_v = (1/6) sum_{t at v} N_t (N_t the triangle's doubled-area normal),
-// which equals (1/6) sum x_{v+1} x x_{v+2} for a closed mesh but needs no
-// absolute coordinates.
+// Positions are FP64; this kernel reads them through the per-marker stencil
+// cache (floor(X) as integers, X - floor(X) rounded once to FP32): the
+// difference of two vertices is (floor_a - floor_b) + (frac_a - frac_b),
+// accurate to FP32 rounding of the difference itself, with no FP64
+// arithmetic (slow on this GPU). All force arithmetic is FP32; the body's
+// total area and volume are reduced in FP64. The volume gradient at a vertex
+// uses the closed-surface form dV/dx_v = (1/6) sum_{t at v} N_t (N_t the
+// triangle's doubled-area normal), which equals (1/6) sum x_{v+1} x x_{v+2}
+// for a closed mesh but needs no absolute coordinates.
 //
-// All membranes share one template mesh, so its topology (16-bit packed) is
-// staged once in the shared memory of a persistent thread block that then
-// works through the bodies, two at a time (one per 512-thread half, with
-// named barriers). Templates too large for that layout use one block per
-// body with the topology read from global memory.
+// One thread block per membrane. Pass A computes every triangle's normal and
+// area and the body's area and volume; pass B adds each edge's stretching
+// and bending forces and each triangle's area and volume forces to the
+// vertices with shared-memory atomics. All membranes share one template
+// mesh; its 16-bit packed topology is read from global memory and stays in
+// the L1 cache.
 //
 // Rigid bodies (Sec. 2.3, penalty reading of the rigid coupling): each marker
 // is tethered to its body-fixed point X^ref = C + R(q) r_k; the fluid receives
@@ -40,8 +40,7 @@ namespace ibm {
 namespace {
 
 constexpr int RIGID_THREADS = 256;
-constexpr int HALF_THREADS = 512;     // threads per body in the persistent membrane kernel
-constexpr int GLOBAL_THREADS = 256;   // threads per body in the fallback membrane kernel
+constexpr int MEMBRANE_THREADS = 256;
 
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
@@ -50,22 +49,13 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-// barrier over the nthr threads of one body's group
-__device__ __forceinline__ void group_sync(int id, int nthr) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
-}
-
-// Views of the packed template topology (in shared or global memory).
+// Views of the packed template topology.
 struct Topo {
   const ushort4* edges;      // (a, b, c, d)
   const ushort2* edge_tris;  // (t1, t2)
   const float2* edge_rest;   // (l0, theta0)
   const ushort4* tris;       // (v0, v1, v2, -)
   const float* area0;
-  const unsigned short* ve_start;  // [nv + 1]
-  const unsigned short* ve;        // (edge << 2) | role
-  const unsigned short* vt_start;  // [nv + 1]
-  const unsigned short* vt;        // (triangle << 2) | slot
 };
 
 __device__ __forceinline__ Topo topo_at(const unsigned char* base, const MeshDev& mesh) {
@@ -75,55 +65,52 @@ __device__ __forceinline__ Topo topo_at(const unsigned char* base, const MeshDev
   T.edge_rest = reinterpret_cast<const float2*>(base + mesh.off_edge_rest);
   T.tris = reinterpret_cast<const ushort4*>(base + mesh.off_tris);
   T.area0 = reinterpret_cast<const float*>(base + mesh.off_area0);
-  T.ve_start = reinterpret_cast<const unsigned short*>(base + mesh.off_ve_start);
-  T.ve = reinterpret_cast<const unsigned short*>(base + mesh.off_ve);
-  T.vt_start = reinterpret_cast<const unsigned short*>(base + mesh.off_vt_start);
-  T.vt = reinterpret_cast<const unsigned short*>(base + mesh.off_vt);
   return T;
 }
 
-// Membrane forces of one body by a group of nthr threads (thread tid in the
-// group, barrier id bar), in three passes over shared memory with no
-// atomics (the result does not depend on thread scheduling):
-//   A. per triangle: N_t = (x1 - x0) x (x2 - x0), A_t; the body's total
-//      area and volume (FP64 group reduction);
-//   B. per edge: the stretching coefficient (dU/dl)/l and the bending
-//      coefficient k_b sin(theta - theta0), theta from the two triangles'
-//      N_t (already the outward normals n1, n2 of the edge's wings);
-//   C. per vertex: the sum over the edges and triangles the vertex belongs
-//      to, using the stored coefficients and normals.
-// work: [6 nv + 4 nt + 2 ne] floats; red: [2 * 32] doubles.
-__device__ void membrane_body(const MarkersDev& m, const BodyDev& B, const MeshDev& mesh, const Topo& T,
-                              float* work, double* red, int tid, int nthr, int bar) {
+}  // namespace
+
+// Membrane forces, one block per body. Dynamic shared memory:
+// [9 nv + 4 nt] words (positions as floor + fraction, force sums, normals, areas).
+__global__ void __launch_bounds__(MEMBRANE_THREADS, 4)
+    k_membranes(MarkersDev m, const BodyDev* __restrict__ bodies, const int* __restrict__ list, MeshDev mesh) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[2 * 32];
+  const BodyDev& B = bodies[list[blockIdx.x]];
+  const Topo T = topo_at(mesh.packed, mesh);
   const size_t M = (size_t)m.M;
   const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
-  float* sH = work;            // [3][nv] hi parts of the offsets from vertex 0
-  float* sL = sH + 3 * nv;     // [3][nv] lo parts
-  float* sN = sL + 3 * nv;     // [3][nt] doubled-area normals
-  float* sA = sN + 3 * nt;     // [nt] areas
-  float* sEs = sA + nt;        // [ne] stretching coefficients
-  float* sEb = sEs + ne;       // [ne] bending coefficients
-  const double ax0 = m.X[B.first], ay0 = m.X[M + B.first], az0 = m.X[2 * M + B.first];
-  for (int v = tid; v < nv; v += nthr) {
-    const int k = B.first + v;
-    const double o[3] = {m.X[k] - ax0, m.X[M + k] - ay0, m.X[2 * M + k] - az0};
+  int* sI = reinterpret_cast<int*>(smem);             // [3][nv] floor(X)
+  float* sR = reinterpret_cast<float*>(sI + 3 * nv);  // [3][nv] X - floor(X)
+  float* sF = sR + 3 * nv;                            // [3][nv] force sums
+  float* sN = sF + 3 * nv;                            // [3][nt] doubled-area normals
+  float* sA = sN + 3 * nt;                            // [nt] areas
+  const int first = B.first;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float hi = (float)o[a];
-      sH[a * nv + v] = hi;
-      sL[a * nv + v] = (float)(o[a] - (double)hi);
+      sI[a * nv + v] = m.cell[a * M + first + v];
+      sR[a * nv + v] = m.frac[a * M + first + v];
+      sF[a * nv + v] = 0.f;
     }
   }
-  group_sync(bar, nthr);
+  __syncthreads();
+  // x_a - x_b, exact in the integer part, one FP32 rounding in the fraction
   auto dv = [&](int a, int b) {
-    return make_float3((sH[a] - sH[b]) + (sL[a] - sL[b]), (sH[nv + a] - sH[nv + b]) + (sL[nv + a] - sL[nv + b]),
-                       (sH[2 * nv + a] - sH[2 * nv + b]) + (sL[2 * nv + a] - sL[2 * nv + b]));
+    return make_float3((float)(sI[a] - sI[b]) + (sR[a] - sR[b]),
+                       (float)(sI[nv + a] - sI[nv + b]) + (sR[nv + a] - sR[nv + b]),
+                       (float)(sI[2 * nv + a] - sI[2 * nv + b]) + (sR[2 * nv + a] - sR[2 * nv + b]));
   };
   auto normal = [&](int t) { return make_float3(sN[t], sN[nt + t], sN[2 * nt + t]); };
+  auto addF = [&](int v, float3 f) {
+    atomicAdd(sF + v, f.x);
+    atomicAdd(sF + nv + v, f.y);
+    atomicAdd(sF + 2 * nv + v, f.z);
+  };
 
   // A. triangle normals and areas, total area and volume
   float a_part = 0.f, v_part = 0.f;
-  for (int t = tid; t < nt; t += nthr) {
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     const ushort4 Tr = T.tris[t];
     const float3 N = cross(dv(Tr.y, Tr.x), dv(Tr.z, Tr.x));
     const float At = 0.5f * sqrtf(dot(N, N));
@@ -132,8 +119,7 @@ __device__ void membrane_body(const MarkersDev& m, const BodyDev& B, const MeshD
     a_part += At;
     // p0 . (p1 x p2) = p0 . ((p1 - p0) x (p2 - p0)), p0 the offset of the
     // triangle's first vertex from vertex 0
-    const float3 p0 = make_float3(sH[Tr.x] + sL[Tr.x], sH[nv + Tr.x] + sL[nv + Tr.x], sH[2 * nv + Tr.x] + sL[2 * nv + Tr.x]);
-    v_part += dot(p0, N) * (1.0f / 6.0f);
+    v_part += dot(dv(Tr.x, 0), N) * (1.0f / 6.0f);
   }
   double s0 = a_part, s1 = v_part;
 #pragma unroll
@@ -141,119 +127,67 @@ __device__ void membrane_body(const MarkersDev& m, const BodyDev& B, const MeshD
     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
   }
-  if ((tid & 31) == 0) {
-    red[2 * (tid >> 5)] = s0;
-    red[2 * (tid >> 5) + 1] = s1;
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = s0;
+    red[2 * (threadIdx.x >> 5) + 1] = s1;
   }
-  group_sync(bar, nthr);  // normals, areas and partial sums are visible
+  __syncthreads();  // normals, areas and partial sums are visible
   double A = 0.0, V = 0.0;
-  for (int w = 0; w < (nthr >> 5); ++w) {
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
     A += red[2 * w];
     V += red[2 * w + 1];
   }
   const float cg = B.k_g * (float)((A - (double)mesh.A0) / (double)mesh.A0);
   const float cv = B.k_v * (float)((V - (double)mesh.V0) / (double)mesh.V0);
 
-  // B. per-edge coefficients
-  for (int e = tid; e < ne; e += nthr) {
+  // B. stretching and bending, per edge
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const ushort4 E = T.edges[e];
-    const ushort2 ET = T.edge_tris[e];
     const float2 rest = T.edge_rest[e];
     const float3 ev = dv(E.y, E.x);  // b - a
     const float L2 = dot(ev, ev), l = sqrtf(L2);
     const float l0 = rest.x, x = l / (2.0f * l0);
     const float kp = 1.25f * B.kBT_p * l0 * l0;  // zero bond force at x = 1/2
     const float dUdl = B.kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
-    sEs[e] = dUdl / l;
-    float sb = 0.f;
-    if (B.k_b != 0.f) {
-      const float3 n1 = normal(ET.x), n2 = normal(ET.y);
-      const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
-      sb = B.k_b * sinf(theta - rest.y);
+    const float3 fs = (dUdl / l) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
+    if (B.k_b == 0.f) {
+      addF(E.x, fs);
+      addF(E.y, (-1.0f) * fs);
+      continue;
     }
-    sEb[e] = sb;
+    // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
+    // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
+    // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
+    const ushort2 ET = T.edge_tris[e];
+    const float3 n1 = normal(ET.x), n2 = normal(ET.y);
+    const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
+    const float sb = B.k_b * sinf(theta - rest.y);
+    const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
+    const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
+    addF(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
+    addF(E.y, (-1.0f) * fs + (sb * t1) * gc + (sb * t2) * gd);
+    addF(E.z, (-sb) * gc);
+    addF(E.w, (-sb) * gd);
   }
-  group_sync(bar, nthr);
-
-  // C. per-vertex gather
-  for (int v = tid; v < nv; v += nthr) {
-    float3 F = make_float3(0.f, 0.f, 0.f);
-    for (int q = T.ve_start[v]; q < T.ve_start[v + 1]; ++q) {
-      const int code = T.ve[q];
-      const int e = code >> 2, role = code & 3;
-      const ushort4 E = T.edges[e];
-      const float3 ev = dv(E.y, E.x);
-      if (role == 0) F = F + sEs[e] * ev;          // stretching: F_a = (dU/dl)/l (b - a)
-      else if (role == 1) F = F + (-sEs[e]) * ev;  // F_b = -F_a
-      const float s = sEb[e];
-      if (s == 0.f) continue;
-      // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
-      // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
-      // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
-      const ushort2 ET = T.edge_tris[e];
-      const float L2 = dot(ev, ev), l = sqrtf(L2);
-      const float3 n1 = normal(ET.x), n2 = normal(ET.y);
-      const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
-      float3 g;
-      if (role == 2) {
-        g = gc;
-      } else if (role == 3) {
-        g = gd;
-      } else {
-        const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
-        g = (role == 0) ? (-(1.0f - t1)) * gc + (-(1.0f - t2)) * gd : (-t1) * gc + (-t2) * gd;
-      }
-      F = F + (-s) * g;
+  // area (local + global) and volume, per triangle
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const ushort4 Tr = T.tris[t];
+    const int vv[3] = {Tr.x, Tr.y, Tr.z};
+    const float3 N = normal(t);
+    const float At = sA[t], At0 = T.area0[t];
+    const float coef = B.k_l * (At - At0) / At0 + cg;
+    const float3 nh = (1.0f / (2.0f * At)) * N;
+    const float3 fV = (-cv / 6.0f) * N;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // F_v = -coef dA_t/dx_v - (k_v (V - V0)/V0) N_t / 6, dA_t/dx_v = 1/2 n x (x_{v+2} - x_{v+1})
+      const float3 gA = cross(nh, dv(vv[(q + 2) % 3], vv[(q + 1) % 3]));
+      addF(vv[q], (-0.5f * coef) * gA + fV);
     }
-    for (int q = T.vt_start[v]; q < T.vt_start[v + 1]; ++q) {
-      const int code = T.vt[q];
-      const int t = code >> 2, slot = code & 3;
-      const ushort4 Tr = T.tris[t];
-      const int vv[3] = {Tr.x, Tr.y, Tr.z};
-      const float3 N = normal(t);
-      // area (local + global): F_v = -coef dA_t/dx_v, dA_t/dx_v = 1/2 n x (x_{v+2} - x_{v+1})
-      const float At0 = T.area0[t];
-      const float coef = B.k_l * (sA[t] - At0) / At0 + cg;
-      const float3 nh = (1.0f / (2.0f * sA[t])) * N;
-      const float3 gA = cross(nh, dv(vv[(slot + 2) % 3], vv[(slot + 1) % 3]));
-      // volume: F_v = -(k_v (V - V0)/V0) dV/dx_v, dV/dx_v = N_t / 6 summed over the triangles at v
-      F = F + (-0.5f * coef) * gA + (-cv / 6.0f) * N;
-    }
-    m.F[B.first + v] = make_float4(F.x, F.y, F.z, 0.f);
-  }
-  group_sync(bar, nthr);  // the work area is reused by the next body
-}
-
-}  // namespace
-
-// Persistent membrane kernel: 2 x HALF_THREADS threads per block, the
-// template topology in shared memory, one body per half at a time.
-__global__ void __launch_bounds__(2 * HALF_THREADS, 1)
-    k_membranes(MarkersDev m, const BodyDev* __restrict__ bodies, const int* __restrict__ list, int n, MeshDev mesh) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[2][2 * 32];
-  // stage the packed topology (16-byte words)
-  {
-    const int4* src = reinterpret_cast<const int4*>(mesh.packed);
-    int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = threadIdx.x; i < mesh.packed_bytes / 16; i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  const Topo T = topo_at(smem, mesh);
-  const int half = threadIdx.x / HALF_THREADS, tid = threadIdx.x % HALF_THREADS;
-  float* work = reinterpret_cast<float*>(smem + mesh.packed_bytes) + (size_t)half * mesh.work_floats;
-  for (int i = 2 * blockIdx.x + half; i < n; i += 2 * gridDim.x)
-    membrane_body(m, bodies[list[i]], mesh, T, work, red[half], tid, HALF_THREADS, 1 + half);
-}
-
-// Fallback: one block per membrane, topology read from global memory.
-__global__ void __launch_bounds__(GLOBAL_THREADS)
-    k_membranes_global(MarkersDev m, const BodyDev* __restrict__ bodies, const int* __restrict__ list, MeshDev mesh) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[2 * 32];
-  const Topo T = topo_at(mesh.packed, mesh);
-  membrane_body(m, bodies[list[blockIdx.x]], mesh, T, reinterpret_cast<float*>(smem), red, threadIdx.x,
-                GLOBAL_THREADS, 1);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x)
+    m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
 }
 
 // One block per rigid body.
@@ -327,31 +261,22 @@ __global__ void __launch_bounds__(RIGID_THREADS)
   B->quat[0] = q0 / nq; B->quat[1] = q1 / nq; B->quat[2] = q2 / nq; B->quat[3] = q3 / nq;
 }
 
-size_t membrane_work_floats(int nv, int nt, int ne) { return (size_t)6 * nv + (size_t)4 * nt + (size_t)2 * ne; }
+size_t membrane_work_floats(int nv, int nt, int ne) {
+  (void)ne;
+  return (size_t)9 * nv + (size_t)4 * nt;
+}
 
-cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem, bool* persistent) {
+cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem) {
   const size_t work = sizeof(float) * mesh.work_floats;
-  const size_t persistent_smem = (size_t)mesh.packed_bytes + 2 * work;
-  *persistent = persistent_smem + 2048 <= max_smem;
-  if (*persistent)
-    return cudaFuncSetAttribute(k_membranes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persistent_smem);
   if (work + 1024 > max_smem) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_membranes_global, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)work);
+  return cudaFuncSetAttribute(k_membranes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)work);
 }
 
 void launch_forces(const MarkersDev& m, BodyDev* bodies, const int* membranes, int n_membranes, const int* rigids,
-                   int n_rigids, const MeshDev& mesh, bool persistent, int n_sm, cudaStream_t st) {
+                   int n_rigids, const MeshDev& mesh, cudaStream_t st) {
   if (n_rigids > 0) k_rigid<<<n_rigids, RIGID_THREADS, 0, st>>>(m, bodies, rigids);
   if (n_membranes == 0) return;
-  const size_t work = sizeof(float) * mesh.work_floats;
-  if (persistent) {
-    int grid = (n_membranes + 1) / 2;
-    if (grid > n_sm) grid = n_sm;
-    k_membranes<<<grid, 2 * HALF_THREADS, (size_t)mesh.packed_bytes + 2 * work, st>>>(m, bodies, membranes,
-                                                                                       n_membranes, mesh);
-  } else {
-    k_membranes_global<<<n_membranes, GLOBAL_THREADS, work, st>>>(m, bodies, membranes, mesh);
-  }
+  k_membranes<<<n_membranes, MEMBRANE_THREADS, sizeof(float) * mesh.work_floats, st>>>(m, bodies, membranes, mesh);
 }
 
 }  // namespace ibm

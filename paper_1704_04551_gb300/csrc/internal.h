@@ -21,11 +21,12 @@ void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* 
 void launch_interpolate(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups,
                         const int4* boxes, cudaStream_t st);
 cudaError_t transfer_configure();
+void launch_stencil_cache(const MarkersDev& m, cudaStream_t st);
 
 // forces.cu
 void launch_forces(const MarkersDev& m, BodyDev* bodies, const int* membranes, int n_membranes, const int* rigids,
-                   int n_rigids, const MeshDev& mesh, bool persistent, int n_sm, cudaStream_t st);
+                   int n_rigids, const MeshDev& mesh, cudaStream_t st);
 size_t membrane_work_floats(int nv, int nt, int ne);
-cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem, bool* persistent);
+cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem);
 
 }  // namespace ibm

@@ -1,16 +1,22 @@
 // Immersed-boundary transfer kernels (Sec. 2.3 of arXiv:1704.04551):
 //   spread       g(x) += F_k delta(x - X_k)          (Eq. ibmForceSpread)
 //   interpolate  U_k = sum_x u(x) delta(x - X_k),    (Eq. ibmVelocityInterpret)
-//                then X_k += U_k (explicit advection, dt = 1)
+//                then X_k += U_k (explicit advection, dt = 1, FP64)
 // with delta(x) = phi(x) phi(y) phi(z), phi(r) = (1 + cos(pi r / 2)) / 4 for
 // |r| <= 2 (Eq. deltaPhiSimple). The 4-point stencil of a marker at X is the
 // nodes floor(X)-1 .. floor(X)+2 on each axis; nodes inside walls or the
 // tube's solid are skipped (no renormalisation). Periodic axes wrap.
 //
+// Positions are FP64, but these kernels read the per-marker stencil cache
+// (floor(X) as integers, X - floor(X) rounded once to FP32), which the
+// interpolation kernel refreshes right after advecting each marker; the only
+// FP64 arithmetic left is that advection.
+//
 // One thread block per marker group (a body, or a run of tracers), four
-// threads per marker (one per x offset of the stencil, so the four read or
-// write consecutive words). The block bounds the group's stencils with a
-// box; when the box fits in shared memory (BOX_CELLS cells):
+// threads per marker: lane a handles the stencil's x offset a, so the four
+// read or write consecutive words, and the y/z weights are computed once and
+// shared by shuffles. The block bounds the group's stencils with a box; when
+// the box fits in shared memory (BOX_CELLS cells):
 //   spreading accumulates there in 32-bit fixed point (native integer
 //   shared-memory atomics; the sum does not depend on the order of the
 //   additions) with a scale chosen from the group's largest force so that no
@@ -32,25 +38,33 @@ namespace ibm {
 namespace {
 
 constexpr int XFER_THREADS = 512;   // two blocks per SM (shared-memory box), 32 warps
-constexpr int BOX_CELLS = 8192;  // 3 floats per cell: 96 KiB of shared memory
+constexpr int BOX_CELLS = 8192;     // 3 words per cell: 96 KiB of shared memory
 
-struct Stencil {
-  int bx, by, bz;        // first node on each axis (unwrapped)
-  float wx[4], wy[4], wz[4];
+__device__ __forceinline__ float phi(float r) { return 0.25f * (1.0f + cospif(0.5f * r)); }
+
+// Stencil of marker k as seen by lane a of its 4-lane group: first node
+// (unwrapped) on each axis, this lane's x weight and the four y and z
+// weights (computed one per lane and shared by shuffles). All 32 lanes of
+// the warp must call this (inactive groups pass any valid k).
+struct LaneStencil {
+  int bx, by, bz;
+  float wx;           // weight of node bx + a
+  float wy[4], wz[4];
 };
-
-// Marker position (FP64) -> stencil base and FP32 weights. The fractional
-// offset s = X - floor(X) is formed in FP64 and rounded once to FP32.
-__device__ __forceinline__ void make_stencil(double X, double Y, double Z, Stencil& s) {
-  const double fx = floor(X), fy = floor(Y), fz = floor(Z);
-  s.bx = (int)fx - 1; s.by = (int)fy - 1; s.bz = (int)fz - 1;
-  const float ox = (float)(X - fx), oy = (float)(Y - fy), oz = (float)(Z - fz);
+__device__ __forceinline__ void lane_stencil(const MarkersDev& m, int k, int a, LaneStencil& s) {
+  const size_t M = (size_t)m.M;
+  s.bx = m.cell[k] - 1;
+  s.by = m.cell[M + k] - 1;
+  s.bz = m.cell[2 * M + k] - 1;
+  const float fx = m.frac[k], fy = m.frac[M + k], fz = m.frac[2 * M + k];
+  // node b + a sits at distance (a - 1) - frac from X
+  s.wx = phi((float)(a - 1) - fx);
+  const float wy_own = phi((float)(a - 1) - fy), wz_own = phi((float)(a - 1) - fz);
+  const int base = threadIdx.x & 28;  // first lane of this 4-lane group within the warp
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    // node b + k sits at distance r = (k - 1) - offset from X
-    s.wx[k] = 0.25f * (1.0f + cospif(0.5f * ((float)(k - 1) - ox)));
-    s.wy[k] = 0.25f * (1.0f + cospif(0.5f * ((float)(k - 1) - oy)));
-    s.wz[k] = 0.25f * (1.0f + cospif(0.5f * ((float)(k - 1) - oz)));
+  for (int b = 0; b < 4; ++b) {
+    s.wy[b] = __shfl_sync(0xffffffffu, wy_own, base + b);
+    s.wz[b] = __shfl_sync(0xffffffffu, wz_own, base + b);
   }
 }
 
@@ -66,51 +80,67 @@ __device__ __forceinline__ bool fluid_row(const LatticeDev& L, int& y, int& z) {
   return !solid_yz(L, y, z);
 }
 
-// Mark the (at most 8) tiles covered by a marker's stencil.
+// Mark the (at most 8) tiles covered by a marker's stencil; within a warp,
+// only one lane stores each distinct tile.
 template <int GEOM>
-__device__ __forceinline__ void mark_tiles(const LatticeDev& L, const Stencil& s) {
-  int tx[2], ty[2], tz[2], nxt = 0, nyt = 0, nzt = 0;
+__device__ __forceinline__ void mark_tiles(const LatticeDev& L, int bx, int by, int bz, bool active) {
+  int tx[2] = {-1, -1}, ty[2] = {-1, -1}, tz[2] = {-1, -1};
+  if (active) {
+    int n = 0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int t = wrapi(s.bx + a, L.nx) >> TILE_X_SHIFT;
-    if (nxt == 0 || tx[nxt - 1] != t) { if (nxt < 2) tx[nxt++] = t; }
+    for (int a = 0; a < 4; ++a) {
+      const int t = wrapi(bx + a, L.nx) >> TILE_X_SHIFT;
+      if (n == 0 || tx[n - 1] != t) { if (n < 2) tx[n++] = t; }
+    }
+    n = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int y = by + a;
+      if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
+      else if ((unsigned)y >= (unsigned)L.ny) continue;
+      const int t = y >> TILE_Y_SHIFT;
+      if (n == 0 || ty[n - 1] != t) { if (n < 2) ty[n++] = t; }
+    }
+    n = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int z = bz + a;
+      if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
+      else if ((unsigned)z >= (unsigned)L.nz) continue;
+      const int t = z >> TILE_Z_SHIFT;
+      if (n == 0 || tz[n - 1] != t) { if (n < 2) tz[n++] = t; }
+    }
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int y = s.by + a;
-    if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
-    else if ((unsigned)y >= (unsigned)L.ny) continue;
-    const int t = y >> TILE_Y_SHIFT;
-    if (nyt == 0 || ty[nyt - 1] != t) { if (nyt < 2) ty[nyt++] = t; }
+  for (int q = 0; q < 8; ++q) {
+    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+    const bool ok = tx[a] >= 0 && ty[b] >= 0 && tz[c] >= 0;
+    const int t = ok ? tx[a] + L.ntx * (ty[b] + L.nty * tz[c]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    if (ok && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) L.flags[t] = 1;
   }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int z = s.bz + a;
-    if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
-    else if ((unsigned)z >= (unsigned)L.nz) continue;
-    const int t = z >> TILE_Z_SHIFT;
-    if (nzt == 0 || tz[nzt - 1] != t) { if (nzt < 2) tz[nzt++] = t; }
-  }
-  for (int c = 0; c < nzt; ++c)
-    for (int b = 0; b < nyt; ++b)
-      for (int a = 0; a < nxt; ++a) L.flags[tx[a] + L.ntx * (ty[b] + L.nty * tz[c])] = 1;
 }
 
-// Bounding box of the group's stencil nodes (unwrapped coordinates):
-// lo = min floor(X) - 1, dims = max floor(X) - min floor(X) + 4.
-__device__ void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, int4& dims) {
+// Bounding box of the group's stencil nodes (unwrapped coordinates) and the
+// group's largest force component.
+__device__ void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, int4& dims, float& fmax) {
   __shared__ int s_lo[3], s_hi[3];
+  __shared__ unsigned s_fmax;
   if (threadIdx.x < 3) {
     s_lo[threadIdx.x] = INT_MAX;
     s_hi[threadIdx.x] = INT_MIN;
   }
+  if (threadIdx.x == 0) s_fmax = 0u;
   __syncthreads();
   const size_t M = (size_t)m.M;
   int lx = INT_MAX, ly = INT_MAX, lz = INT_MAX, hx = INT_MIN, hy = INT_MIN, hz = INT_MIN;
+  float fm = 0.f;
   for (int k = G.first + threadIdx.x; k < G.first + G.count; k += blockDim.x) {
-    const int fx = (int)floor(m.X[k]), fy = (int)floor(m.X[M + k]), fz = (int)floor(m.X[2 * M + k]);
-    lx = min(lx, fx); ly = min(ly, fy); lz = min(lz, fz);
-    hx = max(hx, fx); hy = max(hy, fy); hz = max(hz, fz);
+    const int cx_ = m.cell[k], cy_ = m.cell[M + k], cz_ = m.cell[2 * M + k];
+    lx = min(lx, cx_); ly = min(ly, cy_); lz = min(lz, cz_);
+    hx = max(hx, cx_); hy = max(hy, cy_); hz = max(hz, cz_);
+    const float4 F = m.F[k];
+    fm = fmaxf(fm, fmaxf(fabsf(F.x), fmaxf(fabsf(F.y), fabsf(F.z))));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -120,10 +150,12 @@ __device__ void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, i
     hx = max(hx, __shfl_xor_sync(0xffffffffu, hx, o));
     hy = max(hy, __shfl_xor_sync(0xffffffffu, hy, o));
     hz = max(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+    fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomicMin(&s_lo[0], lx); atomicMin(&s_lo[1], ly); atomicMin(&s_lo[2], lz);
     atomicMax(&s_hi[0], hx); atomicMax(&s_hi[1], hy); atomicMax(&s_hi[2], hz);
+    atomicMax(&s_fmax, __float_as_uint(fm));  // non-negative floats order as their bits
   }
   __syncthreads();
   const long long ex = (long long)s_hi[0] - s_lo[0] + 4, ey = (long long)s_hi[1] - s_lo[1] + 4,
@@ -131,35 +163,38 @@ __device__ void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, i
   lo = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, 0);
   const bool fits = ex > 0 && ey > 0 && ez > 0 && ex * ey * ez <= BOX_CELLS;
   dims = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
+  fmax = __uint_as_float(s_fmax);
+}
+
+// Stencil cache of one coordinate: floor and fractional part.
+__device__ __forceinline__ void cache_coord(const MarkersDev& m, size_t off, double X) {
+  const double f = floor(X);
+  m.cell[off] = (int)f;
+  m.frac[off] = (float)(X - f);
 }
 
 }  // namespace
 
+// Stencil cache from the positions (after set_markers).
+__global__ void k_stencil_cache(MarkersDev m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.M) return;
+  const size_t M = (size_t)m.M;
+  for (int a = 0; a < 3; ++a) cache_coord(m, a * M + k, m.X[a * M + k]);
+}
+
 template <int GEOM>
 __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, MarkersDev m, const MarkerGroup* groups,
-                                                         int4* boxes) {
+                                                            int4* boxes) {
   extern __shared__ __align__(16) int ibox[];  // [3][vol] fixed-point sums
-  __shared__ unsigned s_fmax_bits;
   const MarkerGroup G = groups[blockIdx.x];
   int4 lo, dims;
-  if (threadIdx.x == 0) s_fmax_bits = 0u;
-  group_box(m, G, lo, dims);  // synchronises
+  float fmax;
+  group_box(m, G, lo, dims, fmax);  // synchronises
   if (threadIdx.x == 0) {
     boxes[2 * blockIdx.x] = lo;
     boxes[2 * blockIdx.x + 1] = dims;
   }
-  const size_t M = (size_t)m.M;
-  // largest force component of the group (non-negative floats order as their bits)
-  float fm = 0.f;
-  for (int k = G.first + threadIdx.x; k < G.first + G.count; k += blockDim.x) {
-    const float4 F = m.F[k];
-    fm = fmaxf(fm, fmaxf(fabsf(F.x), fmaxf(fabsf(F.y), fabsf(F.z))));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(&s_fmax_bits, __float_as_uint(fm));
-  __syncthreads();
-  const float fmax = __uint_as_float(s_fmax_bits);
   const bool any_force = fmax > 0.f;
   const bool in_smem = dims.w != 0;
   const int vol = dims.x * dims.y * dims.z;
@@ -171,24 +206,28 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, Marker
     __syncthreads();
   }
   const int a = threadIdx.x & 3;
-  for (int j = threadIdx.x >> 2; j < G.count; j += blockDim.x >> 2) {
-    const int k = G.first + j;
-    Stencil s;
-    make_stencil(m.X[k], m.X[M + k], m.X[2 * M + k], s);
-    if (a == 0) mark_tiles<GEOM>(L, s);
-    if (!any_force) continue;
+  // whole warps iterate together (shuffles inside)
+  for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
+    const int j = j0 + (threadIdx.x >> 2);
+    const bool active = j < G.count;
+    const int k = G.first + (active ? j : 0);
+    LaneStencil s;
+    lane_stencil(m, k, a, s);
+    mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active && a == 0);
+    if (!active || !any_force) continue;
     const float4 F = m.F[k];
     if (in_smem) {
       const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
+      const float fx = F.x * S * s.wx, fy = F.y * S * s.wx, fz = F.z * S * s.wx;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          const float w = s.wx[a] * s.wy[b] * s.wz[c] * S;
+          const float w = s.wy[b] * s.wz[c];
           const int li = li0 + dims.x * (b + dims.y * c);
-          atomicAdd(ibox + li, __float2int_rn(F.x * w));
-          atomicAdd(ibox + vol + li, __float2int_rn(F.y * w));
-          atomicAdd(ibox + 2 * vol + li, __float2int_rn(F.z * w));
+          atomicAdd(ibox + li, __float2int_rn(fx * w));
+          atomicAdd(ibox + vol + li, __float2int_rn(fy * w));
+          atomicAdd(ibox + 2 * vol + li, __float2int_rn(fz * w));
         }
     } else {
       const int x = wrapi(s.bx + a, L.nx);
@@ -198,7 +237,7 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, Marker
         for (int b = 0; b < 4; ++b) {
           int y = s.by + b, z = s.bz + c;
           if (!fluid_row<GEOM>(L, y, z)) continue;
-          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          const float w = s.wx * s.wy[b] * s.wz[c];
           atomicAdd(L.g + L.nx * (y + L.ny * z) + x, make_float4(F.x * w, F.y * w, F.z * w, 0.f));
         }
       }
@@ -220,8 +259,8 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, Marker
 }
 
 template <int GEOM>
-__global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, MarkersDev m, const MarkerGroup* groups,
-                                                              const int4* boxes) {
+__global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, MarkersDev m,
+                                                                 const MarkerGroup* groups, const int4* boxes) {
   extern __shared__ __align__(16) float box[];  // [3][vol]
   const MarkerGroup G = groups[blockIdx.x];
   const int4 lo = boxes[2 * blockIdx.x], dims = boxes[2 * blockIdx.x + 1];
@@ -248,14 +287,12 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
     __syncthreads();
   }
   const int a = threadIdx.x & 3;
-  // every thread of a 4-lane group runs the same iterations (shuffles below)
   for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
     const int j = j0 + (threadIdx.x >> 2);
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
-    const double X = m.X[k], Y = m.X[M + k], Z = m.X[2 * M + k];
-    Stencil s;
-    make_stencil(X, Y, Z, s);
+    LaneStencil s;
+    lane_stencil(m, k, a, s);
     float ux = 0.f, uy = 0.f, uz = 0.f;
     if (in_smem) {
       const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
@@ -263,7 +300,7 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          const float w = s.wy[b] * s.wz[c];
           const int li = li0 + dims.x * (b + dims.y * c);
           ux = fmaf(w, box[li], ux);
           uy = fmaf(w, box[vol + li], uy);
@@ -277,7 +314,7 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
         for (int b = 0; b < 4; ++b) {
           int y = s.by + b, z = s.bz + c;
           if (!fluid_row<GEOM>(L, y, z)) continue;
-          const float w = s.wx[a] * s.wy[b] * s.wz[c];
+          const float w = s.wy[b] * s.wz[c];
           const float4 u = L.uw[L.nx * (y + L.ny * z) + x];
           ux = fmaf(w, u.x, ux);
           uy = fmaf(w, u.y, uy);
@@ -285,6 +322,7 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
         }
       }
     }
+    ux *= s.wx; uy *= s.wx; uz *= s.wx;
     // sum the four x columns of the stencil
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {
@@ -292,11 +330,15 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
       uy += __shfl_xor_sync(0xffffffffu, uy, o);
       uz += __shfl_xor_sync(0xffffffffu, uz, o);
     }
-    if (active && a == 0) {
-      m.U[k] = make_float4(ux, uy, uz, 0.f);
-      m.X[k] = X + (double)ux;
-      m.X[M + k] = Y + (double)uy;
-      m.X[2 * M + k] = Z + (double)uz;
+    if (!active) continue;
+    if (a == 0) m.U[k] = make_float4(ux, uy, uz, 0.f);
+    if (a < 3) {
+      // advection of one coordinate per lane (FP64), then its stencil cache
+      const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
+      const size_t off = (size_t)a * M + k;
+      const double Xn = m.X[off] + (double)ua;
+      m.X[off] = Xn;
+      cache_coord(m, off, Xn);
     }
   }
 }
@@ -309,6 +351,11 @@ cudaError_t transfer_configure() {
   CFG(k_interpolate<GEOM_PERIODIC>); CFG(k_interpolate<GEOM_YWALLS>); CFG(k_interpolate<GEOM_TUBE>);
 #undef CFG
   return e;
+}
+
+void launch_stencil_cache(const MarkersDev& m, cudaStream_t st) {
+  if (m.M == 0) return;
+  k_stencil_cache<<<(m.M + 255) / 256, 256, 0, st>>>(m);
 }
 
 void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups, int4* boxes,
