@@ -197,7 +197,7 @@ def collide_traffic(storage):
         if ':' in line and line.startswith('- '):
             k, v = line[2:].split(':', 1)
             vals[k.strip()] = v.strip().strip('`')
-    if vals.get('lbm.cu sha256[:16]') != sha:
+    if vals.get('lbm.cu sha256 prefix') != sha:
         return None
     try:
         return float(vals['dram bytes per launch (full size)'])

@@ -80,45 +80,47 @@ __device__ __forceinline__ bool fluid_row(const LatticeDev& L, int& y, int& z) {
   return !solid_yz(L, y, z);
 }
 
-// Mark the (at most 8) tiles covered by a marker's stencil; within a warp,
-// only one lane stores each distinct tile.
+// Tiles (at most 2 per axis) covered by a stencil that starts at node b on
+// an axis of n nodes with tile shift sh; periodic axes wrap, others clip.
+template <bool PERIODIC>
+__device__ __forceinline__ int axis_tiles(int b, int n, int sh, int t[2]) {
+  int v = PERIODIC ? wrapi(b, n) : b;
+  int cnt = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a, ++v) {
+    if (PERIODIC && v >= n) v -= n;
+    if (!PERIODIC && (unsigned)v >= (unsigned)n) continue;
+    const int q = v >> sh;
+    if (cnt == 0 || t[cnt - 1] != q) { if (cnt < 2) t[cnt++] = q; }
+  }
+  return cnt;
+}
+
+// Mark the (at most 8) tiles covered by a marker's stencil. Markers of a
+// group are numbered along a space-filling curve, so a marker whose tile set
+// equals that of the marker handled by the previous 4-lane group of the warp
+// skips its stores.
 template <int GEOM>
 __device__ __forceinline__ void mark_tiles(const LatticeDev& L, int bx, int by, int bz, bool active) {
   int tx[2] = {-1, -1}, ty[2] = {-1, -1}, tz[2] = {-1, -1};
-  if (active) {
-    int n = 0;
+  const int nx_ = axis_tiles<true>(bx, L.nx, TILE_X_SHIFT, tx);
+  const int ny_ = GEOM == GEOM_PERIODIC ? axis_tiles<true>(by, L.ny, TILE_Y_SHIFT, ty)
+                                        : axis_tiles<false>(by, L.ny, TILE_Y_SHIFT, ty);
+  const int nz_ = GEOM != GEOM_TUBE ? axis_tiles<true>(bz, L.nz, TILE_Z_SHIFT, tz)
+                                    : axis_tiles<false>(bz, L.nz, TILE_Z_SHIFT, tz);
+  // same tile set as the previous 4-lane group in the warp?
+  const int src = ((int)(threadIdx.x & 31) - 4) & 31;
+  bool same = __shfl_sync(0xffffffffu, (int)active, src) != 0 && (threadIdx.x & 31) >= 4;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int t = wrapi(bx + a, L.nx) >> TILE_X_SHIFT;
-      if (n == 0 || tx[n - 1] != t) { if (n < 2) tx[n++] = t; }
-    }
-    n = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      int y = by + a;
-      if (GEOM == GEOM_PERIODIC) y = wrapi(y, L.ny);
-      else if ((unsigned)y >= (unsigned)L.ny) continue;
-      const int t = y >> TILE_Y_SHIFT;
-      if (n == 0 || ty[n - 1] != t) { if (n < 2) ty[n++] = t; }
-    }
-    n = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      int z = bz + a;
-      if (GEOM != GEOM_TUBE) z = wrapi(z, L.nz);
-      else if ((unsigned)z >= (unsigned)L.nz) continue;
-      const int t = z >> TILE_Z_SHIFT;
-      if (n == 0 || tz[n - 1] != t) { if (n < 2) tz[n++] = t; }
-    }
+  for (int q = 0; q < 2; ++q) {
+    same &= __shfl_sync(0xffffffffu, tx[q], src) == tx[q];
+    same &= __shfl_sync(0xffffffffu, ty[q], src) == ty[q];
+    same &= __shfl_sync(0xffffffffu, tz[q], src) == tz[q];
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
-    const bool ok = tx[a] >= 0 && ty[b] >= 0 && tz[c] >= 0;
-    const int t = ok ? tx[a] + L.ntx * (ty[b] + L.nty * tz[c]) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, t);
-    if (ok && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) L.flags[t] = 1;
-  }
+  if (!active || same) return;
+  for (int c = 0; c < nz_; ++c)
+    for (int b = 0; b < ny_; ++b)
+      for (int a = 0; a < nx_; ++a) L.flags[tx[a] + L.ntx * (ty[b] + L.nty * tz[c])] = 1;
 }
 
 // Bounding box of the group's stencil nodes (unwrapped coordinates) and the
@@ -245,16 +247,23 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, Marker
   }
   if (!in_smem || !any_force) return;
   __syncthreads();
-  // add the nonzero cells of the box to the lattice
+  // add the nonzero cells of the box to the lattice, one warp per box row
   const float inv = 1.0f / S;
-  for (int li = threadIdx.x; li < vol; li += blockDim.x) {
-    const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
-    if ((qx | qy | qz) == 0) continue;
-    const int ax = li % dims.x, t = li / dims.x, ay = t % dims.y, az = t / dims.y;
-    int y = lo.y + ay, z = lo.z + az;
+  const int nrows = dims.y * dims.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int xw0 = wrapi(lo.x, L.nx);
+  for (int r = warp; r < nrows; r += nwarps) {
+    int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
     if (!fluid_row<GEOM>(L, y, z)) continue;
-    atomicAdd(L.g + L.nx * (y + L.ny * z) + wrapi(lo.x + ax, L.nx),
-              make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
+    float4* row = L.g + L.nx * (y + L.ny * z);
+    for (int ax = lane; ax < dims.x; ax += 32) {
+      const int li = r * dims.x + ax;
+      const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
+      if ((qx | qy | qz) == 0) continue;
+      int x = xw0 + ax;
+      if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+      atomicAdd(row + x, make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
+    }
   }
 }
 
@@ -271,13 +280,16 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, M
     // load the box of velocities row by row; solid rows contribute zero
     const int nrows = dims.y * dims.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int xw0 = wrapi(lo.x, L.nx);
     for (int r = warp; r < nrows; r += nwarps) {
       int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
       const bool fl = fluid_row<GEOM>(L, y, z);
       const float4* row = L.uw + L.nx * (y + L.ny * z);
       for (int ax = lane; ax < dims.x; ax += 32) {
         float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (fl) u = row[wrapi(lo.x + ax, L.nx)];
+        int x = xw0 + ax;
+        if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+        if (fl) u = row[x];
         const int li = r * dims.x + ax;
         box[li] = u.x;
         box[vol + li] = u.y;

@@ -191,9 +191,11 @@ def rigid_ellipsoid(center, axes, quat, first, freq=9, kappa=0.02):
 
 
 def shear_ellipsoid(n=32, ny=None, nz=None, tau=0.8, wall_speed=0.02, axes=(6.0, 3.0, 3.0),
-                    seed=1705, kappa=0.02, freq=9, steps=500, quat=None):
+                    seed=1705, kappa=0.02, freq=9, steps=500, quat=None, couette_init=False):
     """Rigid prolate ellipsoid centred in a Couette cell: periodic x and z,
-    y-walls moving at -/+ wall_speed."""
+    y-walls moving at -/+ wall_speed. With couette_init the fluid starts
+    from the linear wall-driven profile u_x = U (2 (y + 1/2)/H - 1) instead
+    of rest (no start-up transient)."""
     ny = ny or n
     nz = nz or n
     rng = np.random.default_rng(seed)
@@ -202,8 +204,15 @@ def shear_ellipsoid(n=32, ny=None, nz=None, tau=0.8, wall_speed=0.02, axes=(6.0,
     X, body = rigid_ellipsoid(center, axes, q, 0, freq=freq, kappa=kappa)
     lattice = dict(nx=n, ny=ny, nz=nz, tau=tau, geometry=GEOM_YWALLS,
                    wall_u=[-wall_speed, wall_speed], tube_radius=0.0, body_force=[0.0, 0.0, 0.0])
-    return dict(name=f'shear_ellipsoid_{n}x{ny}x{nz}', lattice=lattice, mesh=None,
-                bodies=[body], X=X, steps=steps, seed=seed)
+    w = dict(name=f'shear_ellipsoid_{n}x{ny}x{nz}', lattice=lattice, mesh=None,
+             bodies=[body], X=X, steps=steps, seed=seed)
+    if couette_init:
+        y = np.arange(ny, dtype=np.float64)
+        prof = wall_speed * (2.0 * (y + 0.5) / ny - 1.0)
+        u0 = np.zeros((3, nz, ny, n))
+        u0[0] = prof[None, :, None]
+        w['u0'] = u0.reshape(3, -1)
+    return w
 
 
 def rbc_tube(n=256, radius=120.0, n_cells=3000, diameter=16.0, tau=1.0, reynolds=1.0,
