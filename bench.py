@@ -65,6 +65,12 @@ def make_workload(name: str):
         w['storage'] = 'f32'
         w['label'] = 'rbc_tube_64^3_R30_50x642_f32'
         return w
+    if name == 'serve':
+        # the first case of the serving stream (the reference arm's sample)
+        w = I.serving_stream(n_cases=1, seed=1708)[0]
+        w['storage'] = 'f32'
+        w['label'] = 'serving_stream_case0_' + w['name']
+        return w
     if name == 'shear32':
         w = I.shear_ellipsoid(n=32, steps=500)
         w['storage'] = 'f32'
@@ -416,13 +422,207 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# serving: continuous batching of independent shear-cell cases
+# ----------------------------------------------------------------------------
+def serving_cases(args):
+    from paper_1704_04551_gb300 import inputs as I
+    cases = I.serving_stream(n_cases=args.serve_cases, seed=1708, periods=2.0, period_scale=args.period_scale)
+    for w in cases:
+        lat = w['lattice']
+        w['N'] = lat['nx'] * lat['ny'] * lat['nz']
+        w['B_step'] = w['N'] * 38 * 4 + touched_cells(lat, w['X']) * 24 + w['X'].shape[1] * 72
+    return cases
+
+
+def serve_batched(binding, cases, arrivals, args, keep=()):
+    """Run the stream through one server; cases are submitted when their
+    arrival time (seconds after the start) has passed. Returns per-case
+    completion times, the number of chunks and the results of `keep`."""
+    srv = binding.Server(args.serve_budget_gb * 1e9, max_active=args.serve_slots, chunk_steps=args.serve_chunk)
+    n = len(cases)
+    order = sorted(range(n), key=lambda i: arrivals[i])
+    done_t, results, outstanding = [None] * n, {}, {}
+    nxt, chunks, unstable = 0, 0, 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[order[nxt]] <= now:
+            i = order[nxt]
+            outstanding[srv.submit(cases[i], cases[i]['steps'])] = i
+            nxt += 1
+        if not outstanding:
+            if nxt == n:
+                break
+            time.sleep(max(0.0, arrivals[order[nxt]] - now))
+            continue
+        rc, running, pending, _ = srv.advance()
+        chunks += 1
+        unstable += rc != binding.OK
+        now = time.perf_counter() - t0
+        for cid, i in list(outstanding.items()):
+            if srv.poll(cid)[0] == binding.CASE_DONE:
+                done_t[i] = now
+                r = srv.result(cid)
+                if i in keep:
+                    results[i] = r
+                del outstanding[cid]
+    makespan = time.perf_counter() - t0
+    srv.close()
+    return dict(done=done_t, makespan=makespan, chunks=chunks, results=results, unstable=unstable)
+
+
+def serve_sequential(binding, cases, keep=()):
+    """The same cases one at a time in FIFO order through the single-lattice
+    handle (its own kernels and CUDA graphs). Returns per-case service times."""
+    service, results = [], {}
+    for i, w in enumerate(cases):
+        t0 = time.perf_counter()
+        sim = binding.Simulation.from_workload(w)
+        sim.step(w['steps'])
+        rho, u = sim.fields()
+        X, U, _ = sim.markers()
+        sim.close()
+        service.append(time.perf_counter() - t0)
+        if i in keep:
+            results[i] = dict(rho=rho, u=u, X=X, U=U)
+    return service, results
+
+
+def fifo_latency(arrivals, service):
+    """Completion minus arrival of a one-at-a-time FIFO server."""
+    t, lat = 0.0, []
+    for a, s in sorted(zip(arrivals, service)):
+        t = max(t, a) + s
+        lat.append(t - a)
+    return lat
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q))
+
+
+def run_serve(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device('cuda', local)
+    dist = init_dist(ws, 'nccl')
+    from paper_1704_04551_gb300 import binding, build
+    build.build()
+    cases = serving_cases(args)
+    n = len(cases)
+    updates = sum(w['N'] * w['steps'] for w in cases)
+    alg_bytes = sum(w['B_step'] * w['steps'] for w in cases)
+    keep = tuple(range(0, n, max(1, n // 4)))
+
+    # warm-up: the smallest cases through a server, a few chunks each
+    small = sorted(cases, key=lambda w: w['N'])[:3]
+    warm = [dict(w, steps=args.serve_chunk * 2) for w in small]
+    for _ in range(args.warmup):
+        serve_batched(binding, warm, [0.0] * len(warm), args)
+
+    # burst: every case arrives at t = 0
+    clocks = ClockSampler(local)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    time.sleep(0.3)
+    burst = serve_batched(binding, cases, [0.0] * n, args, keep)
+    clk = clocks.stop()
+    burst_s = reduce_max(dist, burst['makespan'], device)
+    capacity = n / burst['makespan']
+
+    # Poisson arrivals at 0.9 x the measured batched capacity
+    rng = np.random.default_rng(1708)
+    arr = np.cumsum(rng.exponential(1.0 / (0.9 * capacity), n))
+    arr -= arr[0]
+    pois = serve_batched(binding, cases, list(arr), args)
+
+    # sequential per-case solves (same GPU, one case at a time, FIFO)
+    service, seq_res = serve_sequential(binding, cases, keep)
+    seq_s = sum(service)
+
+    # equal accuracy: batched and sequential results of sampled cases
+    du = max(float(np.linalg.norm(burst['results'][i]['u'] - seq_res[i]['u']) /
+                   max(np.linalg.norm(seq_res[i]['u']), 1e-300)) for i in keep)
+    dX = max(float(np.abs(burst['results'][i]['X'] - seq_res[i]['X']).max()) for i in keep)
+
+    lat_burst = [t for t in burst['done']]
+    lat_pois = [t - a for t, a in zip(pois['done'], arr)]
+    seq_burst = fifo_latency([0.0] * n, service)
+    seq_pois = fifo_latency(list(arr), service)
+    value = aggregate(updates, burst_s, ws) / 1e6
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / burst['makespan'] / 1e9
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        w0 = cases[0]
+        k = 40
+        r = time_oracle(w0, k)
+        cpu = dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
+                   sample=f'{k} coupled steps of serving case 0 ({w0["name"]}) on one host core (FP64 C oracle)',
+                   seconds=r['seconds'])
+    if rank == 0:
+        h2d = sum(w['X'].nbytes for w in cases)
+        d2h = sum(w['N'] * 4 * 8 + w['X'].nbytes * 2 for w in cases)
+        Ls = [w['lattice']['nx'] for w in cases]
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=burst['chunks'], warmup=args.warmup,
+            ms_per_step=1e3 * burst['makespan'] / burst['chunks'], higher_is_better=True, scaling='weak',
+            vs_baseline=None, dtype='f32', data='synthetic',
+            config=dict(workload=f'serving_stream_{n}cases_{args.period_scale:g}x2T',
+                        cases=n, seed=1708, lattice_L=[min(Ls), max(Ls)], total_lattice_updates=updates,
+                        case_steps=[min(w['steps'] for w in cases), max(w['steps'] for w in cases)],
+                        slots=args.serve_slots, chunk_steps=args.serve_chunk,
+                        step='one server advance = chunk_steps coupled steps of every admitted case',
+                        l2='working set of the admitted cases larger than L2' if sum(w['N'] for w in cases) * 124 > 129e6 else 'working set fits L2',
+                        parallelism=f'replicas x{ws}' if ws > 1 else 'single GPU'),
+            serving=dict(
+                burst=dict(p50_s=pct(lat_burst, 50), p99_s=pct(lat_burst, 99), makespan_s=burst['makespan'],
+                           mlups=updates / burst['makespan'] / 1e6, chunks=burst['chunks']),
+                poisson=dict(rate_per_s=0.9 * capacity, p50_s=pct(lat_pois, 50), p99_s=pct(lat_pois, 99),
+                             makespan_s=pois['makespan'], mlups=updates / pois['makespan'] / 1e6),
+                sequential=dict(mlups=updates / seq_s / 1e6, makespan_s=seq_s,
+                                burst_p50_s=pct(seq_burst, 50), burst_p99_s=pct(seq_burst, 99),
+                                poisson_p50_s=pct(seq_pois, 50), poisson_p99_s=pct(seq_pois, 99),
+                                note='single-lattice handle per case, FIFO; Poisson latencies from the measured service times'),
+                speedup_vs_sequential=seq_s / burst['makespan'],
+                equal_accuracy=dict(max_rel_l2_u=du, max_abs_dX=dX, cases_compared=len(keep)),
+                unstable_cases=burst['unstable'] + pois['unstable']),
+            roofline=dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak, traffic=None,
+                          kernel='whole batched step (all stages, host admission gaps included)',
+                          peak_source=f'{peak_kind} hbm_gbs (burst copy)', alg_bytes=alg_bytes),
+            cpu_baseline=cpu,
+            e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=h2d / burst['chunks'],
+                     d2h_bytes_per_step=d2h / burst['chunks'],
+                     note='serving is end to end by construction: submission copies from host, results are read back to host inside the timed loop'),
+            clocks=dict(sm_mhz=clk['sm_mhz'], sm_max_mhz=clk['sm_max_mhz'], reasons=clk['reasons'],
+                        samples=clk['samples']),
+            gpu_launches=burst['chunks'] * args.serve_chunk * 7 + 4 * n)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=1000)
     ap.add_argument('--warmup', type=int, default=20)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--workload', default='tube256', choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube160', 'tube64', 'shear32'])
+    ap.add_argument('--workload', default='tube256',
+                    choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube160', 'tube64', 'shear32', 'serve'])
+    ap.add_argument('--serve-cases', type=int, default=64)
+    ap.add_argument('--period-scale', type=float, default=0.05)
+    ap.add_argument('--serve-slots', type=int, default=64)
+    ap.add_argument('--serve-chunk', type=int, default=100)
+    ap.add_argument('--serve-budget-gb', type=float, default=64.0)
     ap.add_argument('--storage', default=None, choices=[None, 'f32', 'f16', 'bf16'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--ref-max-steps', type=int, default=2)
@@ -431,6 +631,8 @@ def main(argv=None):
         raise SystemExit('--warmup must be >= 3')
     if args.impl == 'reference':
         return run_reference(args)
+    if args.workload == 'serve':
+        return run_serve(args)
     return run_ours(args)
 
 

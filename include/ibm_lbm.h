@@ -204,6 +204,68 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
 int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps);
 int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]);
 
+/* ---------------------------------------------------------------------------
+ * Serving: many independent simulations on one GPU with continuous batching.
+ * The paper runs one simulation per MPI job; this is the serving pattern of
+ * the GB300 build. Cases are submitted at any time and wait in FIFO order
+ * until the device-memory budget and a slot allow their admission; every
+ * ibm_lbm_server_advance then runs one chunk of steps for all admitted cases
+ * together (one batched launch per stage, replayed as a CUDA graph), retires
+ * the cases that reached their step count (their results are copied to host
+ * memory and their device memory is released) and admits waiting ones. A
+ * case's result is the same as running it alone with ibm_lbm_step. Cases use
+ * FP32 storage.
+ * --------------------------------------------------------------------------- */
+typedef struct ibm_lbm_server ibm_lbm_server_t;
+
+typedef struct {
+  size_t device_mem_budget;  /* bytes of device memory all admitted cases may hold */
+  int32_t max_active;        /* slots (cases advanced together), >= 1 */
+  int32_t chunk_steps;       /* steps per advance, even, >= 2 */
+  int32_t device;            /* CUDA device ordinal */
+} ibm_lbm_server_config;
+
+/* One case: lattice (storage must be IBM_LBM_STORE_F32), initial state
+ * (rho0 [N] / u0 [3][N], either NULL for rest), markers, bodies, mesh (as
+ * ibm_lbm_set_markers) and the number of steps to run. All host arrays are
+ * copied at submission. */
+typedef struct {
+  ibm_lbm_config lattice;
+  const double* rho0;
+  const double* u0;
+  const ibm_lbm_mesh* mesh;
+  int32_t n_bodies;
+  const ibm_lbm_body* bodies;
+  int64_t n_markers;
+  const double* X;
+  int64_t n_steps;
+} ibm_lbm_case;
+
+enum { IBM_LBM_CASE_PENDING = 0, IBM_LBM_CASE_RUNNING = 1, IBM_LBM_CASE_DONE = 2 };
+
+/* alloc / stream as for ibm_lbm_create. Errors: E_ARG, E_NOMEM, E_CUDA. */
+int ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
+                          ibm_lbm_server_t** out);
+int ibm_lbm_server_destroy(ibm_lbm_server_t* s);
+/* Queue a case; *id identifies it. E_ARG for an invalid case or one that can
+ * never fit the memory budget. */
+int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* c, uint64_t* id);
+/* Admit what fits, run one chunk (chunk_steps steps; a case stops exactly
+ * at its step count), retire finished cases; waits for the GPU. Reports the
+ * numbers of running, waiting and finished-not-yet-collected cases (any
+ * pointer may be NULL). E_UNSTABLE if a retired case failed its
+ * conservation check (its result is still kept). */
+int ibm_lbm_server_advance(ibm_lbm_server_t* s, int32_t* n_running, int32_t* n_pending, int32_t* n_done);
+/* State (IBM_LBM_CASE_*) and steps completed of a case. */
+int ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* state, int64_t* steps_done);
+/* Copy a finished case's result into caller memory and forget the case:
+ * rho [N], u [3][N] (moments of the last collision, as ibm_lbm_get_fields),
+ * X, U [3][M], bodies [n_bodies] (pose of rigid bodies); any pointer may be
+ * NULL. E_STATE if the case has not finished. */
+int ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double* u, double* X, double* U,
+                          ibm_lbm_body* bodies, int32_t n_bodies);
+const char* ibm_lbm_server_last_error(const ibm_lbm_server_t* s);
+
 /* Force spreading for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a deployment helper. Some callers

@@ -51,6 +51,19 @@ class Mesh(C.Structure):
                 ('tris', C.c_void_p), ('rest_X', C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [('device_mem_budget', C.c_size_t), ('max_active', C.c_int32), ('chunk_steps', C.c_int32),
+                ('device', C.c_int32)]
+
+
+class Case(C.Structure):
+    _fields_ = [('lattice', Config), ('rho0', C.c_void_p), ('u0', C.c_void_p), ('mesh', C.POINTER(Mesh)),
+                ('n_bodies', C.c_int32), ('bodies', C.c_void_p), ('n_markers', C.c_int64), ('X', C.c_void_p),
+                ('n_steps', C.c_int64)]
+
+
+CASE_PENDING, CASE_RUNNING, CASE_DONE = 0, 1, 2
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -95,6 +108,13 @@ def load():
         'ibm_lbm_device_bytes': ([P], C.c_size_t),
         'ibm_lbm_last_error': ([P], C.c_char_p),
         'ibm_lbm_version': ([], C.c_char_p),
+        'ibm_lbm_server_create': ([C.POINTER(ServerConfig), C.POINTER(Allocator), P, C.POINTER(P)], C.c_int),
+        'ibm_lbm_server_destroy': ([P], C.c_int),
+        'ibm_lbm_server_submit': ([P, C.POINTER(Case), C.POINTER(C.c_uint64)], C.c_int),
+        'ibm_lbm_server_advance': ([P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)], C.c_int),
+        'ibm_lbm_server_poll': ([P, C.c_uint64, C.POINTER(I32), C.POINTER(I64)], C.c_int),
+        'ibm_lbm_server_result': ([P, C.c_uint64, P, P, P, P, P, I32], C.c_int),
+        'ibm_lbm_server_last_error': ([P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -243,6 +263,56 @@ def ibm_lbm_last_error(h):
 
 def ibm_lbm_version():
     return load().ibm_lbm_version().decode()
+
+
+def _server_check(s, rc):
+    if rc != OK:
+        msg = load().ibm_lbm_server_last_error(s)
+        raise IbmLbmError(rc, msg.decode() if msg else '')
+    return rc
+
+
+def ibm_lbm_server_create(cfg: ServerConfig, allocator: Allocator | None, stream: int | None):
+    out = C.c_void_p()
+    rc = load().ibm_lbm_server_create(C.byref(cfg), C.byref(allocator) if allocator else None, stream, C.byref(out))
+    if rc != OK:
+        raise IbmLbmError(rc, 'ibm_lbm_server_create failed')
+    return out
+
+
+def ibm_lbm_server_destroy(s):
+    return load().ibm_lbm_server_destroy(s)
+
+
+def ibm_lbm_server_submit(s, case: Case):
+    cid = C.c_uint64()
+    _server_check(s, load().ibm_lbm_server_submit(s, C.byref(case), C.byref(cid)))
+    return cid.value
+
+
+def ibm_lbm_server_advance(s):
+    """Returns (rc, n_running, n_pending, n_done); rc is OK or E_UNSTABLE."""
+    r, p, d = C.c_int32(), C.c_int32(), C.c_int32()
+    rc = load().ibm_lbm_server_advance(s, C.byref(r), C.byref(p), C.byref(d))
+    if rc not in (OK, E_UNSTABLE):
+        _server_check(s, rc)
+    return rc, r.value, p.value, d.value
+
+
+def ibm_lbm_server_poll(s, cid):
+    st, n = C.c_int32(), C.c_int64()
+    _server_check(s, load().ibm_lbm_server_poll(s, cid, C.byref(st), C.byref(n)))
+    return st.value, n.value
+
+
+def ibm_lbm_server_result(s, cid, rho, u, X, U, bodies_n):
+    arr = (Body * bodies_n)() if bodies_n else None
+    _server_check(s, load().ibm_lbm_server_result(s, cid, _p(rho), _p(u), _p(X), _p(U), arr, bodies_n))
+    return list(arr) if arr is not None else []
+
+
+def ibm_lbm_server_last_error(s):
+    return load().ibm_lbm_server_last_error(s).decode()
 
 
 # ---------------------------------------------------------------------------
@@ -423,3 +493,81 @@ class Simulation:
     @property
     def device_bytes(self):
         return ibm_lbm_device_bytes(self.h)
+
+
+class Server:
+    """Continuous batching of independent simulations on one GPU (wraps an
+    ibm_lbm_server). Cases are workload dicts as for Simulation.from_workload
+    plus a step count."""
+
+    def __init__(self, device_mem_budget, max_active=64, chunk_steps=100, device=0, use_torch=True, stream=None):
+        self._mem = None
+        self._stream_obj = None
+        if use_torch:
+            import torch
+            dev = torch.device('cuda', device)
+            self._mem = TorchMemory(dev)
+            if stream is None:
+                self._stream_obj = torch.cuda.Stream(device=dev)
+                stream = self._stream_obj.cuda_stream
+        cfg = ServerConfig(int(device_mem_budget), int(max_active), int(chunk_steps), int(device))
+        self.device = device
+        self.s = ibm_lbm_server_create(cfg, self._mem.struct if self._mem else None, stream)
+        self.meta = {}
+
+    def close(self):
+        if getattr(self, 's', None):
+            ibm_lbm_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, w: dict, n_steps: int) -> int:
+        lat = w['lattice']
+        N = int(lat['nx']) * int(lat['ny']) * int(lat['nz'])
+        X = _f64(w['X'])
+        keep = [X]
+        case = Case()
+        case.lattice = make_config(lat, 'f32', self.device)
+        for name in ('rho0', 'u0'):
+            if w.get(name) is not None:
+                a = _f64(w[name])
+                keep.append(a)
+                setattr(case, name, a.ctypes.data)
+        mesh = w.get('mesh')
+        if mesh is not None:
+            tris = np.ascontiguousarray(mesh['tris'], dtype=np.int32)
+            rest = _f64(mesh['rest_X'])
+            keep += [tris, rest]
+            m = Mesh(rest.shape[1], tris.shape[0], tris.ctypes.data, rest.ctypes.data)
+            keep.append(m)
+            case.mesh = C.pointer(m)
+        bodies = w.get('bodies', [])
+        barr = (Body * len(bodies))(*[make_body(b) for b in bodies]) if bodies else None
+        keep.append(barr)
+        case.n_bodies = len(bodies)
+        case.bodies = C.cast(barr, C.c_void_p) if barr is not None else None
+        case.n_markers = X.shape[1]
+        case.X = X.ctypes.data
+        case.n_steps = int(n_steps)
+        cid = ibm_lbm_server_submit(self.s, case)  # arrays are copied by the call
+        self.meta[cid] = (N, X.shape[1], len(bodies))
+        return cid
+
+    def advance(self):
+        """One chunk for all admitted cases; returns (rc, running, pending, done)."""
+        return ibm_lbm_server_advance(self.s)
+
+    def poll(self, cid):
+        return ibm_lbm_server_poll(self.s, cid)
+
+    def result(self, cid):
+        N, M, nb = self.meta[cid]
+        rho, u = np.zeros(N), np.zeros((3, N))
+        X, U = np.zeros((3, M)), np.zeros((3, M))
+        bodies = ibm_lbm_server_result(self.s, cid, rho, u, X, U, nb)
+        del self.meta[cid]
+        return dict(rho=rho, u=u, X=X, U=U,
+                    bodies=[dict(center=list(b.center), quat=list(b.quat), vel=list(b.vel), omega=list(b.omega))
+                            for b in bodies])

@@ -13,70 +13,10 @@
 
 #include "../../include/ibm_lbm.h"
 #include "common.cuh"
+#include "handle.h"
 #include "internal.h"
 
 using namespace ibm;
-
-namespace {
-
-constexpr int CHUNK = 16;          // steps per captured chunk graph (even)
-constexpr int MAX_MESH_VERTICES = 4096;
-constexpr int BODY_GROUP = 1024;   // markers per transfer block within a body
-constexpr int TRACER_GROUP = 256;  // markers per transfer block for passive tracers
-
-struct Alloc {
-  void* p;
-  size_t bytes;
-};
-
-}  // namespace
-
-struct ibm_lbm {
-  ibm_lbm_config cfg{};
-  ibm_lbm_allocator alloc{};
-  bool has_alloc = false;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  LatticeDev L{};                 // g / flags fields unused: see lat()
-  float4* gbuf[2] = {nullptr, nullptr};   // force density, by step parity
-  uint8_t* fbuf[2] = {nullptr, nullptr};  // touched-tile flags, by step parity
-  RowInfo* rows = nullptr;        // fluid rows of the lattice
-  int n_rows = 0;
-  std::vector<Alloc> lattice_mem, marker_mem;
-  size_t bytes = 0;
-  // markers
-  MarkersDev m{};
-  int n_bodies = 0;
-  BodyDev* d_bodies = nullptr;
-  std::vector<ibm_lbm_body> h_bodies;
-  MeshDev mesh{};
-  int* membrane_list = nullptr;   // body indices of membranes / rigid bodies
-  int* rigid_list = nullptr;
-  int n_membranes = 0, n_rigids = 0;
-  int n_sm = 0;
-  MarkerGroup* groups = nullptr;  // transfer blocks
-  int n_groups = 0;
-  int4* boxes = nullptr;          // per group: stencil box origin and size
-  bool need_zero_F = false;
-  // state
-  long long steps = 0;
-  bool odd_next = false;          // the array is in the post-even-step layout
-  double* d_diag = nullptr;       // [8]
-  unsigned* d_umax = nullptr;
-  double* h_diag = nullptr;       // pinned [8]
-  unsigned* h_umax = nullptr;     // pinned
-  int* h_status = nullptr;        // pinned
-  bool diag_pending = false;
-  // per-stage timing (events between stages, direct launches)
-  std::vector<cudaEvent_t> events;  // 5 per timed step
-  std::vector<char> timed_odd;      // AA parity of each timed step
-  size_t timed_steps = 0;
-  bool timing = false;
-  // graphs
-  cudaGraphExec_t g_chunk = nullptr;
-  cudaGraphExec_t g_single[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  std::string err;
-};
 
 namespace {
 

@@ -1,264 +1,23 @@
-// Marker forces of the immersed bodies.
-//
-// Membranes (Sec. 2.2 of arXiv:1704.04551): F = -dU/dX of Eq.
-// membrane-potential, with
-//   U_stretch = sum_j [ (kBT l_m / 4p)(3x^2 - 2x^3)/(1 - x) + k_p / l_j ]   (Eq. inPlanePotential)
-//               x = l/l_m, l_m = 2 l0 per edge, k_p = 1.25 (kBT/p) l0^2 so that
-//               the bond force vanishes at x = 1/2;
-//   U_bend    = sum_edges k_b (1 - cos(theta - theta0))                     (Eq. bendingEnergy)
-//               theta = signed angle between the outward normals of the two
-//               triangles sharing the edge (positive where convex);
-//   U_area    = k_g (A - A0)^2 / (2 A0) + sum_t k_l (A_t - A_t0)^2/(2 A_t0) (Eq. areaEnergy)
-//   U_volume  = k_v (V - V0)^2 / (2 V0)                                    (Eq. volumeEnergy)
-// Positions are FP64; this kernel reads them through the per-marker stencil
-// cache (floor(X) as integers, X - floor(X) rounded once to FP32): the
-// difference of two vertices is (floor_a - floor_b) + (frac_a - frac_b),
-// accurate to FP32 rounding of the difference itself, with no FP64
-// arithmetic (slow on this GPU). All force arithmetic is FP32; the body's
-// total area and volume are reduced in FP64. The volume gradient at a vertex
-// uses the closed-surface form dV/dx_v = (1/6) sum_{t at v} N_t (N_t the
-// triangle's doubled-area normal), which equals (1/6) sum x_{v+1} x x_{v+2}
-// for a closed mesh but needs no absolute coordinates.
-//
-// One thread block per membrane. Pass A computes every triangle's normal and
-// area and the body's area and volume; pass B adds each edge's stretching
-// and bending forces and each triangle's area and volume forces to the
-// vertices with shared-memory atomics. All membranes share one template
-// mesh; its 16-bit packed topology is read from global memory and stays in
-// the L1 cache.
-//
-// Rigid bodies (Sec. 2.3, penalty reading of the rigid coupling): each marker
-// is tethered to its body-fixed point X^ref = C + R(q) r_k; the fluid receives
-// F_k = -kappa (X_k - X^ref); the body receives the reaction, whose force and
-// torque drive one explicit Newton-Euler step in FP64:
-//   V += F/m; C += V;  w_b += I^-1 (T_b - w_b x I w_b);  q += (0, w)q/2, |q| = 1.
+// Marker-force kernels of one lattice: membranes (Sec. 2.2) one block per
+// body, rigid bodies (Sec. 2.3) one block per body; the bodies and their
+// design notes are in forces_body.cuh.
 #include "common.cuh"
+#include "forces_body.cuh"
 #include "internal.h"
 
 namespace ibm {
 
-namespace {
-
-constexpr int RIGID_THREADS = 256;
-constexpr int MEMBRANE_THREADS = 256;
-
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross(float3 a, float3 b) {
-  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-
-// Views of the packed template topology.
-struct Topo {
-  const ushort4* edges;      // (a, b, c, d)
-  const ushort2* edge_tris;  // (t1, t2)
-  const float2* edge_rest;   // (l0, theta0)
-  const ushort4* tris;       // (v0, v1, v2, -)
-  const float* area0;
-};
-
-__device__ __forceinline__ Topo topo_at(const unsigned char* base, const MeshDev& mesh) {
-  Topo T;
-  T.edges = reinterpret_cast<const ushort4*>(base + mesh.off_edges);
-  T.edge_tris = reinterpret_cast<const ushort2*>(base + mesh.off_edge_tris);
-  T.edge_rest = reinterpret_cast<const float2*>(base + mesh.off_edge_rest);
-  T.tris = reinterpret_cast<const ushort4*>(base + mesh.off_tris);
-  T.area0 = reinterpret_cast<const float*>(base + mesh.off_area0);
-  return T;
-}
-
-}  // namespace
-
-// Membrane forces, one block per body. Dynamic shared memory:
-// [9 nv + 4 nt] words (positions as floor + fraction, force sums, normals, areas).
 __global__ void __launch_bounds__(MEMBRANE_THREADS, 4)
     k_membranes(MarkersDev m, const BodyDev* __restrict__ bodies, const int* __restrict__ list, MeshDev mesh) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * 32];
-  const BodyDev& B = bodies[list[blockIdx.x]];
-  const Topo T = topo_at(mesh.packed, mesh);
-  const size_t M = (size_t)m.M;
-  const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
-  int* sI = reinterpret_cast<int*>(smem);             // [3][nv] floor(X)
-  float* sR = reinterpret_cast<float*>(sI + 3 * nv);  // [3][nv] X - floor(X)
-  float* sF = sR + 3 * nv;                            // [3][nv] force sums
-  float* sN = sF + 3 * nv;                            // [3][nt] doubled-area normals
-  float* sA = sN + 3 * nt;                            // [nt] areas
-  const int first = B.first;
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sI[a * nv + v] = m.cell[a * M + first + v];
-      sR[a * nv + v] = m.frac[a * M + first + v];
-      sF[a * nv + v] = 0.f;
-    }
-  }
-  __syncthreads();
-  // x_a - x_b, exact in the integer part, one FP32 rounding in the fraction
-  auto dv = [&](int a, int b) {
-    return make_float3((float)(sI[a] - sI[b]) + (sR[a] - sR[b]),
-                       (float)(sI[nv + a] - sI[nv + b]) + (sR[nv + a] - sR[nv + b]),
-                       (float)(sI[2 * nv + a] - sI[2 * nv + b]) + (sR[2 * nv + a] - sR[2 * nv + b]));
-  };
-  auto normal = [&](int t) { return make_float3(sN[t], sN[nt + t], sN[2 * nt + t]); };
-  auto addF = [&](int v, float3 f) {
-    atomicAdd(sF + v, f.x);
-    atomicAdd(sF + nv + v, f.y);
-    atomicAdd(sF + 2 * nv + v, f.z);
-  };
-
-  // A. triangle normals and areas, total area and volume
-  float a_part = 0.f, v_part = 0.f;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    const ushort4 Tr = T.tris[t];
-    const float3 N = cross(dv(Tr.y, Tr.x), dv(Tr.z, Tr.x));
-    const float At = 0.5f * sqrtf(dot(N, N));
-    sN[t] = N.x; sN[nt + t] = N.y; sN[2 * nt + t] = N.z;
-    sA[t] = At;
-    a_part += At;
-    // p0 . (p1 x p2) = p0 . ((p1 - p0) x (p2 - p0)), p0 the offset of the
-    // triangle's first vertex from vertex 0
-    v_part += dot(dv(Tr.x, 0), N) * (1.0f / 6.0f);
-  }
-  double s0 = a_part, s1 = v_part;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[2 * (threadIdx.x >> 5)] = s0;
-    red[2 * (threadIdx.x >> 5) + 1] = s1;
-  }
-  __syncthreads();  // normals, areas and partial sums are visible
-  double A = 0.0, V = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    A += red[2 * w];
-    V += red[2 * w + 1];
-  }
-  const float cg = B.k_g * (float)((A - (double)mesh.A0) / (double)mesh.A0);
-  const float cv = B.k_v * (float)((V - (double)mesh.V0) / (double)mesh.V0);
-
-  // B. stretching and bending, per edge
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const ushort4 E = T.edges[e];
-    const float2 rest = T.edge_rest[e];
-    const float3 ev = dv(E.y, E.x);  // b - a
-    const float L2 = dot(ev, ev), l = sqrtf(L2);
-    const float l0 = rest.x, x = l / (2.0f * l0);
-    const float kp = 1.25f * B.kBT_p * l0 * l0;  // zero bond force at x = 1/2
-    const float dUdl = B.kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
-    const float3 fs = (dUdl / l) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
-    if (B.k_b == 0.f) {
-      addF(E.x, fs);
-      addF(E.y, (-1.0f) * fs);
-      continue;
-    }
-    // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
-    // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
-    // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
-    const ushort2 ET = T.edge_tris[e];
-    const float3 n1 = normal(ET.x), n2 = normal(ET.y);
-    const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
-    const float sb = B.k_b * sinf(theta - rest.y);
-    const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
-    const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
-    addF(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
-    addF(E.y, (-1.0f) * fs + (sb * t1) * gc + (sb * t2) * gd);
-    addF(E.z, (-sb) * gc);
-    addF(E.w, (-sb) * gd);
-  }
-  // area (local + global) and volume, per triangle
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    const ushort4 Tr = T.tris[t];
-    const int vv[3] = {Tr.x, Tr.y, Tr.z};
-    const float3 N = normal(t);
-    const float At = sA[t], At0 = T.area0[t];
-    const float coef = B.k_l * (At - At0) / At0 + cg;
-    const float3 nh = (1.0f / (2.0f * At)) * N;
-    const float3 fV = (-cv / 6.0f) * N;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // F_v = -coef dA_t/dx_v - (k_v (V - V0)/V0) N_t / 6, dA_t/dx_v = 1/2 n x (x_{v+2} - x_{v+1})
-      const float3 gA = cross(nh, dv(vv[(q + 2) % 3], vv[(q + 1) % 3]));
-      addF(vv[q], (-0.5f * coef) * gA + fV);
-    }
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x)
-    m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+  membrane_block(m, bodies[list[blockIdx.x]], mesh, smem, red);
 }
 
-// One block per rigid body.
-__global__ void __launch_bounds__(RIGID_THREADS)
-    k_rigid(MarkersDev m, BodyDev* __restrict__ bodies, const int* __restrict__ list) {
+__global__ void __launch_bounds__(RIGID_THREADS) k_rigid(MarkersDev m, BodyDev* __restrict__ bodies,
+                                                         const int* __restrict__ list) {
   __shared__ double sh[6 * 32];
-  BodyDev* B = bodies + list[blockIdx.x];
-  const size_t M = (size_t)m.M;
-  double R[3][3];
-  {
-    const double w = B->quat[0], x = B->quat[1], y = B->quat[2], z = B->quat[3];
-    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
-    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
-    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
-  }
-  const double C0 = B->center[0], C1 = B->center[1], C2 = B->center[2];
-  const double kappa = B->kappa;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = B->first + threadIdx.x; k < B->first + B->count; k += blockDim.x) {
-    const double r0 = m.ref[k], r1 = m.ref[M + k], r2 = m.ref[2 * M + k];
-    const double w0 = R[0][0] * r0 + R[0][1] * r1 + R[0][2] * r2;
-    const double w1 = R[1][0] * r0 + R[1][1] * r1 + R[1][2] * r2;
-    const double w2 = R[2][0] * r0 + R[2][1] * r1 + R[2][2] * r2;
-    const double d0 = m.X[k] - (C0 + w0), d1 = m.X[M + k] - (C1 + w1), d2 = m.X[2 * M + k] - (C2 + w2);
-    m.F[k] = make_float4((float)(-kappa * d0), (float)(-kappa * d1), (float)(-kappa * d2), 0.f);
-    const double f0 = kappa * d0, f1 = kappa * d1, f2 = kappa * d2;
-    acc[0] += f0; acc[1] += f1; acc[2] += f2;
-    acc[3] += w1 * f2 - w2 * f1;
-    acc[4] += w2 * f0 - w0 * f2;
-    acc[5] += w0 * f1 - w1 * f0;
-  }
-  // block reduction of the body's force and torque
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 6; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  if (lane == 0)
-    for (int k = 0; k < 6; ++k) sh[k * 32 + warp] = acc[k];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int k = 0; k < 6; ++k) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[k * 32 + w];
-    acc[k] = s;
-  }
-  for (int a = 0; a < 3; ++a) {
-    B->vel[a] += acc[a] / B->mass;
-    B->center[a] += B->vel[a];
-  }
-  double wb[3], tb[3], Iw[3];
-  for (int a = 0; a < 3; ++a) {
-    wb[a] = R[0][a] * B->omega[0] + R[1][a] * B->omega[1] + R[2][a] * B->omega[2];
-    tb[a] = R[0][a] * acc[3] + R[1][a] * acc[4] + R[2][a] * acc[5];
-  }
-  for (int a = 0; a < 3; ++a) Iw[a] = B->inertia[a] * wb[a];
-  const double g0 = wb[1] * Iw[2] - wb[2] * Iw[1];
-  const double g1 = wb[2] * Iw[0] - wb[0] * Iw[2];
-  const double g2 = wb[0] * Iw[1] - wb[1] * Iw[0];
-  wb[0] += (tb[0] - g0) / B->inertia[0];
-  wb[1] += (tb[1] - g1) / B->inertia[1];
-  wb[2] += (tb[2] - g2) / B->inertia[2];
-  for (int a = 0; a < 3; ++a) B->omega[a] = R[a][0] * wb[0] + R[a][1] * wb[1] + R[a][2] * wb[2];
-  const double w = B->quat[0], x = B->quat[1], y = B->quat[2], z = B->quat[3];
-  const double ox = B->omega[0], oy = B->omega[1], oz = B->omega[2];
-  const double q0 = w + 0.5 * (-ox * x - oy * y - oz * z);
-  const double q1 = x + 0.5 * (ox * w + oy * z - oz * y);
-  const double q2 = y + 0.5 * (-ox * z + oy * w + oz * x);
-  const double q3 = z + 0.5 * (ox * y - oy * x + oz * w);
-  const double nq = sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-  B->quat[0] = q0 / nq; B->quat[1] = q1 / nq; B->quat[2] = q2 / nq; B->quat[3] = q3 / nq;
+  rigid_block(m, bodies + list[blockIdx.x], sh);
 }
 
 size_t membrane_work_floats(int nv, int nt, int ne) {

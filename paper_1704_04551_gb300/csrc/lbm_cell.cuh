@@ -1,0 +1,175 @@
+// Device-side bodies of the lattice-Boltzmann kernels, shared by the
+// single-lattice kernels (lbm.cu) and the batched serving kernels
+// (serve.cu). Method: Sec. 2.1 of arXiv:1704.04551 — Eq. lbm (stream + BGK
+// collide + force term), Eq. BGKequilibrium, Eq. rho_u (moments with the
+// half-force shift), the Guo term F_i, Eq. viscosity (tau).
+//
+// AA pattern (one array, each cell reads and writes the same 19 slots):
+//   even step: f_i(x) is read from A[x][i]; the post-collision f*_i(x) is
+//              written to A[x][opp(i)] (a bounced value carries the
+//              moving-wall term already);
+//   odd step:  f_i(x) is read from A[x - c_i][opp(i)] (from A[x][i] when
+//              x - c_i is solid); f*_i(x) is written to A[x + c_i][i], or,
+//              when x + c_i is solid, bounced to A[x][opp(i)].
+// After an odd step the array holds f(t+1) in the natural layout.
+// Populations are stored as deviations d_i = f_i - w_i (scaled in FP16/BF16)
+// and all arithmetic is FP32 in deviation form, which keeps the O(u)
+// information of f_i ~ w_i in the significand.
+#pragma once
+#include "common.cuh"
+
+namespace ibm {
+
+namespace lbm_detail {
+
+template <int S>
+struct Pop {
+  using St = Store<S>;
+  using T = typename St::T;
+  __device__ static __forceinline__ float ld(const T* p, int i) {
+    if constexpr (S == STORE_F32) return *p;
+    else if constexpr (S == STORE_F16) return __half2float(*p) * (1.0f / dev_scale(i));
+    else return __bfloat162float(*p) * (1.0f / dev_scale(i));
+  }
+  __device__ static __forceinline__ void st(T* p, int i, float v) {
+    if constexpr (S == STORE_F32) *p = v;
+    else if constexpr (S == STORE_F16) *p = __float2half_rn(v * dev_scale(i));
+    else *p = __float2bfloat16_rn(v * dev_scale(i));
+  }
+};
+
+struct Cell {
+  int x, y, z;
+  unsigned smask;          // bit (cy+1)*3 + (cz+1): neighbour in that (y,z) direction is solid
+  int oxp, oxm, oyp, oym, ozp, ozm;  // wrapped element offsets of the six axis neighbours
+};
+
+template <int GEOM>
+__device__ __forceinline__ bool make_cell(const LatticeDev& L, int idx, Cell& c) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  c.x = idx % nx;
+  const int t = idx / nx;
+  c.y = t % ny;
+  c.z = t / ny;
+  c.smask = 0u;
+  if constexpr (GEOM != GEOM_PERIODIC) {
+    if (solid_yz(L, c.y, c.z)) return false;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+        if (solid_yz(L, c.y + dy, c.z + dz)) c.smask |= 1u << ((dy + 1) * 3 + (dz + 1));
+  }
+  c.oxp = (c.x == nx - 1) ? -(nx - 1) : 1;
+  c.oxm = (c.x == 0) ? (nx - 1) : -1;
+  const int sy = nx, sz = nx * ny;
+  c.oyp = (c.y == ny - 1) ? -(ny - 1) * sy : sy;
+  c.oym = (c.y == 0) ? (ny - 1) * sy : -sy;
+  c.ozp = (c.z == nz - 1) ? -(nz - 1) * sz : sz;
+  c.ozm = (c.z == 0) ? (nz - 1) * sz : -sz;
+  return true;
+}
+
+// element offset of the neighbour x + s*c_i
+__device__ __forceinline__ int nb_off(const Cell& c, int i, int s) {
+  const int dx = s * cx(i), dy = s * cy(i), dz = s * cz(i);
+  return (dx > 0 ? c.oxp : (dx < 0 ? c.oxm : 0)) + (dy > 0 ? c.oyp : (dy < 0 ? c.oym : 0)) +
+         (dz > 0 ? c.ozp : (dz < 0 ? c.ozm : 0));
+}
+// is x + s*c_i solid?
+__device__ __forceinline__ bool nb_solid(const Cell& c, int i, int s) {
+  return (c.smask >> ((s * cy(i) + 1) * 3 + (s * cz(i) + 1))) & 1u;
+}
+
+}  // namespace lbm_detail
+using namespace lbm_detail;
+
+// One fluid cell of the fused collide-stream-force step (x in the row R).
+template <int S, int ODD, int GEOM, bool DENSE>
+__device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo& R, int x) {
+  using P = Pop<S>;
+  using T = typename P::T;
+  const int idx = R.base + x;
+  Cell c;
+  c.x = x;
+  c.y = R.y;
+  c.smask = (unsigned)R.smask;
+  c.oxp = (x == L.nx - 1) ? 1 - L.nx : 1;
+  c.oxm = (x == 0) ? L.nx - 1 : -1;
+  c.oyp = R.oyp; c.oym = R.oym; c.ozp = R.ozp; c.ozm = R.ozm;
+  T* A = reinterpret_cast<T*>(L.pop);
+  const size_t N = (size_t)L.N;
+
+  // f_j(x) sits at A[x][j] (even step) or at A[x - c_j][opp(j)] (odd step;
+  // A[x][j] if x - c_j is solid). In both parities f*_i(x) goes back to the
+  // slot that held f_opp(i)(x), which covers streaming and half-way
+  // bounce-back alike.
+  float d[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1)))
+      d[j] = P::ld(A + (size_t)j * N + idx, j);
+    else
+      d[j] = P::ld(A + (size_t)opp(j) * N + (idx + nb_off(c, j, -1)), opp(j));
+  }
+
+  // moments (Eq. rho_u): rho = sum f, rho u = sum f c + g/2
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += d[i];
+    if (cx(i)) jx += cx(i) * d[i];
+    if (cy(i)) jy += cy(i) * d[i];
+    if (cz(i)) jz += cz(i) * d[i];
+  }
+  float Gx = L.g0x, Gy = L.g0y, Gz = L.g0z;
+  const int tile = R.trow + (x >> TILE_X_SHIFT);
+  const bool touched = L.flags[tile] != 0;
+  if (touched) {
+    const float4 gg = L.g[idx];
+    Gx += gg.x; Gy += gg.y; Gz += gg.z;
+  }
+  if (L.flags_next[tile]) L.g_next[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float rho = 1.0f + drho;
+  const float irho = 1.0f / rho;
+  const float ux = (jx + 0.5f * Gx) * irho;
+  const float uy = (jy + 0.5f * Gy) * irho;
+  const float uz = (jz + 0.5f * Gz) * irho;
+  if (DENSE || touched) L.uw[idx] = make_float4(ux, uy, uz, drho);
+
+  // BGK relaxation toward the equilibrium (Eq. BGKequilibrium) plus the Guo term
+  const float om = L.omega, pre = L.guo_pre;
+  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const float uG = ux * Gx + uy * Gy + uz * Gz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float w = wgt(i);
+    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float cG = cx(i) * Gx + cy(i) * Gy + cz(i) * Gz;
+    const float deq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
+    const float Fi = pre * w * (3.0f * (cG - uG) + 9.0f * cu * cG);
+    d[i] = d[i] + om * (deq - d[i]) + Fi;
+  }
+
+  // Recompute the write addresses from a few laundered registers instead of
+  // keeping the 19 read addresses alive across the collision (which spills).
+  int widx = idx;
+  asm volatile("" : "+r"(widx), "+r"(c.oxp), "+r"(c.oxm), "+r"(c.oyp), "+r"(c.oym), "+r"(c.ozp), "+r"(c.ozm),
+               "+r"(c.smask));
+  // streaming with half-way bounce-back (moving-wall term on y walls)
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float v = d[i];
+    const bool sol = (GEOM != GEOM_PERIODIC) && i != 0 && nb_solid(c, i, +1);
+    if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
+      const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
+      v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
+    }
+    if (!ODD || i == 0 || sol)
+      P::st(A + (size_t)opp(i) * N + widx, opp(i), v);
+    else
+      P::st(A + (size_t)i * N + (widx + nb_off(c, i, +1)), i, v);
+  }
+}
+
+}  // namespace ibm
