@@ -376,12 +376,20 @@ def jeffery_period(gamma, r):
     return 2.0 * math.pi / gamma * (r + 1.0 / r)
 
 
+def ellipsoid_area(a, b, c):
+    """Surface area of an ellipsoid, Thomsen's approximation (relative error
+    below 1.1 %)."""
+    p = 1.6075
+    return 4.0 * math.pi * (((a * b) ** p + (a * c) ** p + (b * c) ** p) / 3.0) ** (1.0 / p)
+
+
 def serving_stream(n_cases=512, seed=1708, periods=2.0, L_min=24, L_max=96, rate=None,
                    period_scale=1.0, tau=0.8, kappa=0.02, freq=9):
     """Independent rigid-ellipsoid shear cells arriving by a seeded Poisson
     process. L ~ U{L_min..L_max}, aspect r ~ U[1.5, 5], shear rate
     gamma ~ logU[1e-4, 1e-3]; a = 0.1875 L, b = c = max(a / r, 1.5).
-    Each runs ceil(periods * period_scale * T) steps. ``rate`` is the mean
+    Each runs ceil(periods * period_scale * T) steps; the tether stiffness per
+    marker scales with the body's surface area. ``rate`` is the mean
     arrival rate in cases per second (None: all arrive at t = 0)."""
     rng = np.random.default_rng(seed)
     cases = []
@@ -394,8 +402,13 @@ def serving_stream(n_cases=512, seed=1708, periods=2.0, L_min=24, L_max=96, rate
         b = max(a / r, 1.5)
         wall = 0.5 * gamma * L
         steps = int(math.ceil(periods * period_scale * jeffery_period(gamma, a / b)))
+        # the same penalty stiffness per unit surface area as the 6 x 3 x 3
+        # body with `kappa` per marker: with a fixed marker count a thin body
+        # packs its markers ~0.3 lu apart and a fixed per-marker kappa makes
+        # the explicit coupling unstable
+        k_m = kappa * ellipsoid_area(a, b, b) / ellipsoid_area(6.0, 3.0, 3.0)
         case = shear_ellipsoid(n=L, tau=tau, wall_speed=wall, axes=(a, b, b),
-                               seed=seed * 1000 + k, kappa=kappa, freq=freq, steps=steps)
+                               seed=seed * 1000 + k, kappa=k_m, freq=freq, steps=steps)
         if rate is not None:
             t += float(rng.exponential(1.0 / rate))
         case['arrival'] = t

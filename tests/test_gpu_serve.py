@@ -55,27 +55,40 @@ def _serve(cases, max_active, budget=1 << 34, chunk=8):
     return out, most
 
 
-def _same(a, b):
-    for k in ('rho', 'u', 'X', 'U'):
-        assert np.array_equal(a[k], b[k]), k
-    for ba, bb in zip(a['bodies'], b['bodies']):
-        for k in ('center', 'quat', 'vel', 'omega'):
-            assert ba[k] == bb[k], k
+def _same(a, b, exact):
+    """Bit-identical where one marker group covers all markers. Several
+    groups add their boxes into the force density with float atomics, so a
+    cell two groups reach sums in either order and its bits may differ at
+    rounding level from run to run (batched or not): there the bound is
+    1e-6 relative L2 on u and 1e-7 lu on marker positions (FP32 rounding of
+    U ~ 1e-3 over ~50 advection steps, amplified by the stiff membranes)."""
+    if exact:
+        for k in ('rho', 'u', 'X', 'U'):
+            assert np.array_equal(a[k], b[k]), k
+        for ba, bb in zip(a['bodies'], b['bodies']):
+            for k in ('center', 'quat', 'vel', 'omega'):
+                assert ba[k] == bb[k], k
+        return
+    assert rel_l2(a['u'], b['u']) < 1e-6
+    assert rel_l2(a['rho'], b['rho']) < 1e-7
+    assert np.abs(a['X'] - b['X']).max() < 1e-7
 
 
 def test_case_alone_equals_case_in_mix(cuda_lib):
     """The batched kernels run each case's own arithmetic on its own arrays:
     alone, batched with all others, or admitted late behind a two-slot limit,
-    a case's result is bit-identical."""
+    a case's result is the same (bit-identical for the single-group rigid
+    ellipsoids)."""
     cases = _mix()
+    exact = [True, False, False, True]
     alone = [_serve([c], 1)[0][0] for c in cases]
     mixed, most = _serve(cases, 8)
     assert most == len(cases)
     queued, most2 = _serve(cases, 2)
     assert most2 == 2
-    for a, m, q in zip(alone, mixed, queued):
-        _same(a, m)
-        _same(a, q)
+    for a, m, q, e in zip(alone, mixed, queued, exact):
+        _same(a, m, e)
+        _same(a, q, e)
 
 
 def test_served_case_matches_handle_and_oracle(cuda_lib):
@@ -91,7 +104,7 @@ def test_served_case_matches_handle_and_oracle(cuda_lib):
         rho_h, u_h = sim.fields()
         X_h, U_h, _ = sim.markers()
         assert rel_l2(r['u'], u_h) < 1e-6
-        assert np.abs(r['X'] - X_h).max() < 1e-9
+        assert np.abs(r['X'] - X_h).max() < 1e-7
         ora = O.Oracle.from_workload(w)
         ora.step(n)
         fl = fluid_mask(w['lattice'])
