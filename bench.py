@@ -190,11 +190,19 @@ def measured_peaks():
     return 6800.0, 'fallback'
 
 
+def collide_source_sha():
+    """Hash of the sources the collide kernel is built from."""
+    h = hashlib.sha256()
+    for name in ('common.cuh', 'lbm_cell.cuh', 'lbm.cu'):
+        with open(os.path.join(ROOT, 'paper_1704_04551_gb300', 'csrc', name), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def collide_traffic(storage):
     """DRAM bytes per collide launch from the committed ncu summary, if the
     kernel source is unchanged since it was taken."""
-    src = os.path.join(ROOT, 'paper_1704_04551_gb300', 'csrc', 'lbm.cu')
-    sha = hashlib.sha256(open(src, 'rb').read()).hexdigest()[:16]
+    sha = collide_source_sha()
     p = os.path.join(ROOT, 'profiles', f'collide_tube256_{storage}.md')
     if not os.path.exists(p):
         return None
@@ -203,7 +211,7 @@ def collide_traffic(storage):
         if ':' in line and line.startswith('- '):
             k, v = line[2:].split(':', 1)
             vals[k.strip()] = v.strip().strip('`')
-    if vals.get('lbm.cu sha256 prefix') != sha:
+    if vals.get('collide source sha256 prefix') != sha:
         return None
     try:
         return float(vals['dram bytes per launch (full size)'])

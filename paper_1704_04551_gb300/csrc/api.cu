@@ -687,6 +687,10 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     D.work_floats = (int)membrane_work_floats(D.nv, D.nt, D.ne);
     D.A0 = (float)hm.A0;
     D.V0 = (float)hm.V0;
+    int most = 1;  // contributions a vertex receives: its edge roles and triangles
+    for (int v = 0; v < D.nv; ++v)
+      most = std::max(most, hm.v_edge_start[v + 1] - hm.v_edge_start[v] + hm.v_tri_start[v + 1] - hm.v_tri_start[v]);
+    D.qcap = (float)((2147483647.0 - 4096.0) / (double)most);
     int dev = 0, optin = 0;
     CUDA_TRY(h, cudaGetDevice(&dev));
     CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));

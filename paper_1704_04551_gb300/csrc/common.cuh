@@ -132,6 +132,7 @@ struct BodyDev {
   float kBT_p, k_b, k_l, k_g, k_v;
   double kappa, mass, inertia[3];
   double center[3], quat[4], vel[3], omega[3];
+  float qmax;  // membranes: largest force contribution component of the last step (0: none yet)
 };
 
 struct MeshDev {
@@ -145,8 +146,10 @@ struct MeshDev {
   const unsigned char* packed;
   int packed_bytes;  // multiple of 16
   int off_edges, off_edge_tris, off_edge_rest, off_tris, off_area0, off_ve_start, off_ve, off_vt_start, off_vt;
-  int work_floats;   // per-body shared work area: 6 nv + 4 nt + 2 ne floats
+  int work_floats;   // per-body shared work area: 9 nv + 4 nt words
   float A0, V0;
+  float qcap;        // fixed-point force scatter: largest |contribution| in units, such
+                     // that a vertex's sum of all its contributions fits in int32
 };
 
 struct MarkersDev {

@@ -8,10 +8,10 @@
 namespace ibm {
 
 __global__ void __launch_bounds__(MEMBRANE_THREADS, 4)
-    k_membranes(MarkersDev m, const BodyDev* __restrict__ bodies, const int* __restrict__ list, MeshDev mesh) {
+    k_membranes(MarkersDev m, BodyDev* __restrict__ bodies, const int* __restrict__ list, MeshDev mesh) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * 32];
-  membrane_block(m, bodies[list[blockIdx.x]], mesh, smem, red);
+  membrane_block(m, bodies + list[blockIdx.x], mesh, smem, red);
 }
 
 __global__ void __launch_bounds__(RIGID_THREADS) k_rigid(MarkersDev m, BodyDev* __restrict__ bodies,

@@ -25,7 +25,7 @@
 // One thread block per membrane. Pass A computes every triangle's normal and
 // area and the body's area and volume; pass B adds each edge's stretching
 // and bending forces and each triangle's area and volume forces to the
-// vertices with shared-memory atomics. All membranes share one template
+// vertices with shared-memory atomics (fixed point, see membrane_block). All membranes share one template
 // mesh; its 16-bit packed topology is read from global memory and stays in
 // the L1 cache.
 //
@@ -76,25 +76,39 @@ using namespace forces_detail;
 // Membrane forces of one body by the whole thread block. smem: [9 nv + 4 nt]
 // words (positions as floor + fraction, force sums, normals, areas);
 // red: [2 * 32] doubles.
-__device__ __forceinline__ void membrane_block(const MarkersDev& m, const BodyDev& B, const MeshDev& mesh,
+//
+// The force sums are scattered with shared-memory integer atomics in fixed
+// point (native and order-independent; float atomics on shared memory are
+// several times slower): each contribution is scaled by S = qcap / (4 q),
+// q the body's largest contribution component of the previous step, so that
+// contributions up to four times larger than last step's fit in qcap units
+// and no vertex sum can overflow. A block that meets a larger contribution,
+// or has no previous step, redoes the scatter with float atomics. The
+// quantum 1/S is ~3e-8 q, below the FP32 rounding of the sums.
+__device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp, const MeshDev& mesh,
                                                unsigned char* smem, double* red) {
   const Topo T = topo_at(mesh.packed, mesh);
   const size_t M = (size_t)m.M;
   const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
+  const float kBT_p = Bp->kBT_p, k_b = Bp->k_b, k_l = Bp->k_l, k_g = Bp->k_g, k_v = Bp->k_v;
+  const float q_prev = Bp->qmax;
   int* sI = reinterpret_cast<int*>(smem);             // [3][nv] floor(X)
   float* sR = reinterpret_cast<float*>(sI + 3 * nv);  // [3][nv] X - floor(X)
-  float* sF = sR + 3 * nv;                            // [3][nv] force sums
-  float* sN = sF + 3 * nv;                            // [3][nt] doubled-area normals
+  int* sQ = reinterpret_cast<int*>(sR + 3 * nv);      // [3][nv] force sums (fixed point, or float bits)
+  float* sN = reinterpret_cast<float*>(sQ + 3 * nv);  // [3][nt] doubled-area normals
   float* sA = sN + 3 * nt;                            // [nt] areas
-  const int first = B.first;
+  __shared__ float s_dev[2];
+  __shared__ unsigned s_qmax;
+  const int first = Bp->first;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       sI[a * nv + v] = m.cell[a * M + first + v];
       sR[a * nv + v] = m.frac[a * M + first + v];
-      sF[a * nv + v] = 0.f;
+      sQ[a * nv + v] = 0;
     }
   }
+  if (threadIdx.x == 0) s_qmax = 0u;
   __syncthreads();
   // x_a - x_b, exact in the integer part, one FP32 rounding in the fraction
   auto dv = [&](int a, int b) {
@@ -103,11 +117,6 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, const BodyDe
                        (float)(sI[2 * nv + a] - sI[2 * nv + b]) + (sR[2 * nv + a] - sR[2 * nv + b]));
   };
   auto normal = [&](int t) { return make_float3(sN[t], sN[nt + t], sN[2 * nt + t]); };
-  auto addF = [&](int v, float3 f) {
-    atomicAdd(sF + v, f.x);
-    atomicAdd(sF + nv + v, f.y);
-    atomicAdd(sF + 2 * nv + v, f.z);
-  };
 
   // A. triangle normals and areas, total area and volume
   float a_part = 0.f, v_part = 0.f;
@@ -133,62 +142,112 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, const BodyDe
     red[2 * (threadIdx.x >> 5) + 1] = s1;
   }
   __syncthreads();  // normals, areas and partial sums are visible
-  double A = 0.0, V = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    A += red[2 * w];
-    V += red[2 * w + 1];
-  }
-  const float cg = B.k_g * (float)((A - (double)mesh.A0) / (double)mesh.A0);
-  const float cv = B.k_v * (float)((V - (double)mesh.V0) / (double)mesh.V0);
-
-  // B. stretching and bending, per edge
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const ushort4 E = T.edges[e];
-    const float2 rest = T.edge_rest[e];
-    const float3 ev = dv(E.y, E.x);  // b - a
-    const float L2 = dot(ev, ev), l = sqrtf(L2);
-    const float l0 = rest.x, x = l / (2.0f * l0);
-    const float kp = 1.25f * B.kBT_p * l0 * l0;  // zero bond force at x = 1/2
-    const float dUdl = B.kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
-    const float3 fs = (dUdl / l) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
-    if (B.k_b == 0.f) {
-      addF(E.x, fs);
-      addF(E.y, (-1.0f) * fs);
-      continue;
+  if (threadIdx.x == 0) {
+    // A - A0 and V - V0 in FP64 (small differences of large sums)
+    double A = 0.0, V = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      A += red[2 * w];
+      V += red[2 * w + 1];
     }
-    // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
-    // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
-    // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
-    const ushort2 ET = T.edge_tris[e];
-    const float3 n1 = normal(ET.x), n2 = normal(ET.y);
-    const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
-    const float sb = B.k_b * sinf(theta - rest.y);
-    const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
-    const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
-    addF(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
-    addF(E.y, (-1.0f) * fs + (sb * t1) * gc + (sb * t2) * gd);
-    addF(E.z, (-sb) * gc);
-    addF(E.w, (-sb) * gd);
-  }
-  // area (local + global) and volume, per triangle
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    const ushort4 Tr = T.tris[t];
-    const int vv[3] = {Tr.x, Tr.y, Tr.z};
-    const float3 N = normal(t);
-    const float At = sA[t], At0 = T.area0[t];
-    const float coef = B.k_l * (At - At0) / At0 + cg;
-    const float3 nh = (1.0f / (2.0f * At)) * N;
-    const float3 fV = (-cv / 6.0f) * N;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // F_v = -coef dA_t/dx_v - (k_v (V - V0)/V0) N_t / 6, dA_t/dx_v = 1/2 n x (x_{v+2} - x_{v+1})
-      const float3 gA = cross(nh, dv(vv[(q + 2) % 3], vv[(q + 1) % 3]));
-      addF(vv[q], (-0.5f * coef) * gA + fV);
-    }
+    s_dev[0] = (float)(A - (double)mesh.A0) / mesh.A0;
+    s_dev[1] = (float)(V - (double)mesh.V0) / mesh.V0;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x)
-    m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+  const float cg = k_g * s_dev[0];
+  const float cv = k_v * s_dev[1];
+
+  // B. stretching and bending per edge, area and volume per triangle, each
+  // contribution handed to `add`
+  float qmax = 0.f;  // largest contribution component seen by this thread
+  auto pass_b = [&](auto&& add) {
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const ushort4 E = T.edges[e];
+      const float2 rest = T.edge_rest[e];
+      const float3 ev = dv(E.y, E.x);  // b - a
+      const float L2 = dot(ev, ev), l = sqrtf(L2);
+      const float l0 = rest.x, x = l / (2.0f * l0);
+      const float kp = 1.25f * kBT_p * l0 * l0;  // zero bond force at x = 1/2
+      const float dUdl = kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
+      const float3 fs = (dUdl / l) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
+      if (k_b == 0.f) {
+        add(E.x, fs);
+        add(E.y, (-1.0f) * fs);
+        continue;
+      }
+      // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
+      // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
+      // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
+      const ushort2 ET = T.edge_tris[e];
+      const float3 n1 = normal(ET.x), n2 = normal(ET.y);
+      const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
+      const float sb = k_b * sinf(theta - rest.y);
+      const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
+      const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
+      add(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
+      add(E.y, (-1.0f) * fs + (sb * t1) * gc + (sb * t2) * gd);
+      add(E.z, (-sb) * gc);
+      add(E.w, (-sb) * gd);
+    }
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      const ushort4 Tr = T.tris[t];
+      const int vv[3] = {Tr.x, Tr.y, Tr.z};
+      const float3 N = normal(t);
+      const float At = sA[t], At0 = T.area0[t];
+      const float coef = k_l * (At - At0) / At0 + cg;
+      const float3 nh = (1.0f / (2.0f * At)) * N;
+      const float3 fV = (-cv / 6.0f) * N;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        // F_v = -coef dA_t/dx_v - (k_v (V - V0)/V0) N_t / 6, dA_t/dx_v = 1/2 n x (x_{v+2} - x_{v+1})
+        const float3 gA = cross(nh, dv(vv[(q + 2) % 3], vv[(q + 1) % 3]));
+        add(vv[q], (-0.5f * coef) * gA + fV);
+      }
+    }
+  };
+  const float S = q_prev > 0.f ? mesh.qcap / (4.0f * q_prev) : 0.f;
+  bool over = !(q_prev > 0.f);
+  if (!over) {
+    pass_b([&](int v, float3 f) {
+      const float c = fmaxf(fabsf(f.x), fmaxf(fabsf(f.y), fabsf(f.z)));
+      qmax = fmaxf(qmax, c);
+      if (!(c * S <= mesh.qcap)) {  // also catches non-finite values
+        over = true;
+        return;
+      }
+      atomicAdd(sQ + v, __float2int_rn(f.x * S));
+      atomicAdd(sQ + nv + v, __float2int_rn(f.y * S));
+      atomicAdd(sQ + 2 * nv + v, __float2int_rn(f.z * S));
+    });
+  }
+  const bool fallback = __syncthreads_or(over) != 0;
+  if (fallback) {
+    float* sF = reinterpret_cast<float*>(sQ);
+    for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) sF[i] = 0.f;
+    __syncthreads();
+    pass_b([&](int v, float3 f) {
+      qmax = fmaxf(qmax, fmaxf(fabsf(f.x), fmaxf(fabsf(f.y), fabsf(f.z))));
+      atomicAdd(sF + v, f.x);
+      atomicAdd(sF + nv + v, f.y);
+      atomicAdd(sF + 2 * nv + v, f.z);
+    });
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_qmax, __float_as_uint(qmax));  // non-negative floats order as their bits
+  __syncthreads();
+  if (fallback) {
+    const float* sF = reinterpret_cast<const float*>(sQ);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+      m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+  } else {
+    const float inv = 1.0f / S;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+      m.F[first + v] = make_float4((float)sQ[v] * inv, (float)sQ[nv + v] * inv, (float)sQ[2 * nv + v] * inv, 0.f);
+  }
+  if (threadIdx.x == 0) {
+    const float q = __uint_as_float(s_qmax);
+    Bp->qmax = isfinite(q) ? q : 0.f;
+  }
 }
 
 // Tether forces and Newton-Euler update of one rigid body by the whole

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(MEMBRANE_THREADS, 4) k_membranes_b(const CaseD
   const Item it = items[blockIdx.x];
   const CaseDev& C = cases[it.c];
   if (!C.active) return;
-  membrane_block(C.m, C.bodies[it.i], C.mesh, smem, red);
+  membrane_block(C.m, C.bodies + it.i, C.mesh, smem, red);
 }
 
 __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_spread_b(const CaseDev* cases, const Item* items) {

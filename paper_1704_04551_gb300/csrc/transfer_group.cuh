@@ -125,6 +125,53 @@ __device__ __forceinline__ void mark_tiles(const LatticeDev& L, int bx, int by, 
       for (int a = 0; a < nx_; ++a) L.flags[tx[a] + L.ntx * (ty[b] + L.nty * tz[c])] = 1;
 }
 
+// Tiles covered by nodes lo .. lo + n - 1 (unwrapped) of an axis of `size`
+// nodes with tile shift sh, as at most two ranges [t0, t1] of tile indices;
+// periodic axes wrap, others clip. Returns the number of ranges.
+template <bool PERIODIC>
+__device__ __forceinline__ int axis_tile_ranges(int lo, int n, int size, int sh, int2 r[2]) {
+  if (PERIODIC) {
+    if (n >= size) {
+      r[0] = make_int2(0, (size - 1) >> sh);
+      return 1;
+    }
+    const int s = wrapi(lo, size), e = s + n - 1;
+    if (e < size) {
+      r[0] = make_int2(s >> sh, e >> sh);
+      return 1;
+    }
+    r[0] = make_int2(s >> sh, (size - 1) >> sh);
+    r[1] = make_int2(0, (e - size) >> sh);
+    return 2;
+  }
+  const int s = max(lo, 0), e = min(lo + n - 1, size - 1);
+  if (s > e) return 0;
+  r[0] = make_int2(s >> sh, e >> sh);
+  return 1;
+}
+
+// Mark every tile that intersects the box [lo, lo + dims) by the whole
+// block: a superset of the tiles the group's stencils touch, at a cost of a
+// few stores per group.
+template <int GEOM>
+__device__ __forceinline__ void mark_box_tiles(const LatticeDev& L, int4 lo, int4 dims) {
+  int2 rx[2], ry[2], rz[2];
+  const int nrx = axis_tile_ranges<true>(lo.x, dims.x, L.nx, TILE_X_SHIFT, rx);
+  const int nry = GEOM == GEOM_PERIODIC ? axis_tile_ranges<true>(lo.y, dims.y, L.ny, TILE_Y_SHIFT, ry)
+                                        : axis_tile_ranges<false>(lo.y, dims.y, L.ny, TILE_Y_SHIFT, ry);
+  const int nrz = GEOM != GEOM_TUBE ? axis_tile_ranges<true>(lo.z, dims.z, L.nz, TILE_Z_SHIFT, rz)
+                                    : axis_tile_ranges<false>(lo.z, dims.z, L.nz, TILE_Z_SHIFT, rz);
+  for (int iz = 0; iz < nrz; ++iz)
+    for (int iy = 0; iy < nry; ++iy)
+      for (int ix = 0; ix < nrx; ++ix) {
+        const int ax = rx[ix].y - rx[ix].x + 1, ay = ry[iy].y - ry[iy].x + 1, az = rz[iz].y - rz[iz].x + 1;
+        for (int i = threadIdx.x; i < ax * ay * az; i += blockDim.x) {
+          const int tx = rx[ix].x + i % ax, ty = ry[iy].x + (i / ax) % ay, tz = rz[iz].x + i / (ax * ay);
+          L.flags[tx + L.ntx * (ty + L.nty * tz)] = 1;
+        }
+      }
+}
+
 // Bounding box of the group's stencil nodes (unwrapped coordinates) and the
 // group's largest force component.
 __device__ inline void group_box(const MarkersDev& m, const MarkerGroup& G, int4& lo, int4& dims, float& fmax) {
@@ -194,6 +241,8 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   }
   const bool any_force = fmax > 0.f;
   const bool in_smem = dims.w != 0;
+  // touched tiles: from the box when it fits, else marker by marker below
+  if (in_smem) mark_box_tiles<GEOM>(L, lo, dims);
   const int vol = dims.x * dims.y * dims.z;
   // |sum| in any cell <= count * fmax / 8 (delta <= 1/8); map that bound to 2^30
   const float bound = fmax * (float)G.count * 0.125f;
@@ -205,12 +254,14 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   const int a = threadIdx.x & 3;
   // whole warps iterate together (shuffles inside)
   for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
+    if (j0 + ((threadIdx.x >> 5) << 3) >= G.count) continue;  // the whole warp is past the group's end
+    if (in_smem && !any_force) break;
     const int j = j0 + (threadIdx.x >> 2);
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
     LaneStencil s;
     lane_stencil(m, k, a, s);
-    mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active && a == 0);
+    if (!in_smem) mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active && a == 0);
     if (!active || !any_force) continue;
     const float4 F = m.F[k];
     if (in_smem) {
@@ -272,28 +323,40 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
   const int vol = dims.x * dims.y * dims.z;
   if (in_smem) {
     // load the box of velocities row by row; solid rows contribute zero
+    // one warp per box row, four rows in flight per lane (the loads are
+    // latency-bound: the rows are short)
+    constexpr int RIF = 4;
     const int nrows = dims.y * dims.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int xw0 = wrapi(lo.x, L.nx);
-    for (int r = warp; r < nrows; r += nwarps) {
-      int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
-      const bool fl = fluid_row<GEOM>(L, y, z);
-      const float4* row = L.uw + L.nx * (y + L.ny * z);
-      for (int ax = lane; ax < dims.x; ax += 32) {
-        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-        int x = xw0 + ax;
-        if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
-        if (fl) u = row[x];
-        const int li = r * dims.x + ax;
-        box[li] = u.x;
-        box[vol + li] = u.y;
-        box[2 * vol + li] = u.z;
+    for (int ax = lane; ax < dims.x; ax += 32) {
+      int x = xw0 + ax;
+      if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+      for (int r0 = warp; r0 < nrows; r0 += RIF * nwarps) {
+        float4 u[RIF];
+#pragma unroll
+        for (int q = 0; q < RIF; ++q) {
+          const int r = r0 + q * nwarps;
+          u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
+          if (r < nrows && fluid_row<GEOM>(L, y, z)) u[q] = L.uw[(size_t)L.nx * (y + L.ny * z) + x];
+        }
+#pragma unroll
+        for (int q = 0; q < RIF; ++q) {
+          const int r = r0 + q * nwarps;
+          if (r >= nrows) continue;
+          const int li = r * dims.x + ax;
+          box[li] = u[q].x;
+          box[vol + li] = u[q].y;
+          box[2 * vol + li] = u[q].z;
+        }
       }
     }
     __syncthreads();
   }
   const int a = threadIdx.x & 3;
   for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
+    if (j0 + ((threadIdx.x >> 5) << 3) >= G.count) continue;  // the whole warp is past the group's end
     const int j = j0 + (threadIdx.x >> 2);
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
