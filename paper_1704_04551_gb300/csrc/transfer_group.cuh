@@ -224,6 +224,27 @@ __device__ __forceinline__ void cache_coord(const MarkersDev& m, size_t off, dou
   m.frac[off] = (float)(X - f);
 }
 
+// Lane mapping of a row-by-row sweep over a box whose rows hold dx cells:
+// rows shorter than a warp are packed rpw to a warp (lane -> sub-row sub,
+// offset ax); longer rows take one warp each, lanes striding by 32.
+struct RowSweep {
+  int rpw, sub, ax;
+  bool on;
+};
+__device__ __forceinline__ RowSweep row_sweep(int dx) {
+  const int lane = threadIdx.x & 31;
+  RowSweep w;
+  if (dx >= 32 || dx <= 0) {
+    w.rpw = 1; w.sub = 0; w.ax = lane; w.on = true;
+  } else {
+    w.rpw = 32 / dx;
+    w.sub = lane / dx;
+    w.ax = lane - w.sub * dx;
+    w.on = w.sub < w.rpw;
+  }
+  return w;
+}
+
 }  // namespace xfer_detail
 using namespace xfer_detail;
 
@@ -293,22 +314,23 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   }
   if (!in_smem || !any_force) return;
   __syncthreads();
-  // add the nonzero cells of the box to the lattice, one warp per box row
+  // add the nonzero cells of the box to the lattice, row by row
   const float inv = 1.0f / S;
   const int nrows = dims.y * dims.z;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const RowSweep sw = row_sweep(dims.x);
   const int xw0 = wrapi(lo.x, L.nx);
-  for (int r = warp; r < nrows; r += nwarps) {
-    int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
-    if (!fluid_row<GEOM>(L, y, z)) continue;
-    float4* row = L.g + L.nx * (y + L.ny * z);
-    for (int ax = lane; ax < dims.x; ax += 32) {
+  for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
+    int x = xw0 + ax;
+    if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+    for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += nwarps * sw.rpw) {
       const int li = r * dims.x + ax;
       const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
       if ((qx | qy | qz) == 0) continue;
-      int x = xw0 + ax;
-      if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
-      atomicAdd(row + x, make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
+      int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
+      if (!fluid_row<GEOM>(L, y, z)) continue;
+      atomicAdd(L.g + (size_t)L.nx * (y + L.ny * z) + x,
+                make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
     }
   }
 }
@@ -327,23 +349,25 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     // latency-bound: the rows are short)
     constexpr int RIF = 4;
     const int nrows = dims.y * dims.z;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const RowSweep sw = row_sweep(dims.x);
+    const int rstep = nwarps * sw.rpw;
     const int xw0 = wrapi(lo.x, L.nx);
-    for (int ax = lane; ax < dims.x; ax += 32) {
+    for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
       int x = xw0 + ax;
       if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
-      for (int r0 = warp; r0 < nrows; r0 += RIF * nwarps) {
+      for (int r0 = (threadIdx.x >> 5) * sw.rpw + sw.sub; r0 < nrows; r0 += RIF * rstep) {
         float4 u[RIF];
 #pragma unroll
         for (int q = 0; q < RIF; ++q) {
-          const int r = r0 + q * nwarps;
+          const int r = r0 + q * rstep;
           u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
           int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
           if (r < nrows && fluid_row<GEOM>(L, y, z)) u[q] = L.uw[(size_t)L.nx * (y + L.ny * z) + x];
         }
 #pragma unroll
         for (int q = 0; q < RIF; ++q) {
-          const int r = r0 + q * nwarps;
+          const int r = r0 + q * rstep;
           if (r >= nrows) continue;
           const int li = r * dims.x + ax;
           box[li] = u[q].x;
