@@ -217,6 +217,12 @@ __device__ inline void group_box(const MarkersDev& m, const MarkerGroup& G, int4
   fmax = __uint_as_float(s_fmax);
 }
 
+// Round-to-nearest-even of |v| <= 2^22 to an integer with one full-rate add:
+// v + 1.5 * 2^23 has a fixed exponent, so its low mantissa bits hold
+// round(v) + 2^22 (the float-to-int conversion unit runs at a quarter of the
+// FP32 rate).
+__device__ __forceinline__ int to_fixed(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+
 // Stencil cache of one coordinate: floor and fractional part.
 __device__ __forceinline__ void cache_coord(const MarkersDev& m, size_t off, double X) {
   const double f = floor(X);
@@ -265,9 +271,10 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   // touched tiles: from the box when it fits, else marker by marker below
   if (in_smem) mark_box_tiles<GEOM>(L, lo, dims);
   const int vol = dims.x * dims.y * dims.z;
-  // |sum| in any cell <= count * fmax / 8 (delta <= 1/8); map that bound to 2^30
-  const float bound = fmax * (float)G.count * 0.125f;
-  const float S = any_force ? fminf(1073741824.0f / bound, 1e30f) : 0.f;
+  // Fixed-point scale: a contribution is at most fmax / 8 (delta <= 1/8) and
+  // a cell's sum at most count * fmax / 8; S keeps contributions below 2^22
+  // (converted exactly by to_fixed) and sums below 2^30.
+  const float S = any_force ? fminf(33554432.0f, 8589934592.0f / (float)G.count) / fmax : 0.f;
   if (in_smem && any_force) {
     for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
     __syncthreads();
@@ -294,9 +301,9 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
         for (int b = 0; b < 4; ++b) {
           const float w = s.wy[b] * s.wz[c];
           const int li = li0 + dims.x * (b + dims.y * c);
-          atomicAdd(ibox + li, __float2int_rn(fx * w));
-          atomicAdd(ibox + vol + li, __float2int_rn(fy * w));
-          atomicAdd(ibox + 2 * vol + li, __float2int_rn(fz * w));
+          atomicAdd(ibox + li, to_fixed(fx * w));
+          atomicAdd(ibox + vol + li, to_fixed(fy * w));
+          atomicAdd(ibox + 2 * vol + li, to_fixed(fz * w));
         }
     } else {
       const int x = wrapi(s.bx + a, L.nx);
