@@ -4,7 +4,8 @@
 Targets: relative L2 error of the fluid velocity over fluid cells <= 1e-5
 with FP32 population storage and <= 1e-3 with FP16 deviation storage; BF16
 deviation storage (8-bit significand, ~4e-3 rounding per store) is
-reported and held to a loose bound (measured 3.1e-2 after 1000 steps). Also reported: relative L2 of the marker forces, the largest marker
+reported and held to a loose bound (measured 3.1e-2 after 1000 steps).
+Also reported: relative L2 of the marker forces, the largest marker
 displacement error, and the drift of the total mass (FP64 sums)."""
 import numpy as np
 import pytest
