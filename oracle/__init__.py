@@ -40,7 +40,7 @@ class _Body(C.Structure):
                 ('kBT_p', C.c_double), ('k_b', C.c_double), ('k_l', C.c_double), ('k_g', C.c_double),
                 ('k_v', C.c_double), ('kappa', C.c_double), ('mass', C.c_double),
                 ('inertia', C.c_double * 3), ('center', C.c_double * 3), ('quat', C.c_double * 4),
-                ('vel', C.c_double * 3), ('omega', C.c_double * 3)]
+                ('vel', C.c_double * 3), ('omega', C.c_double * 3), ('l0', C.c_double)]
 
 
 _lib = None
@@ -84,6 +84,13 @@ def lib():
         L.ora_mesh_rest.argtypes = [P, P]
         L.ora_shear_modulus.restype = C.c_double
         L.ora_shear_modulus.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.ora_filament_energy.restype = C.c_double
+        L.ora_filament_energy.argtypes = [P, C.c_int32, P]
+        L.ora_filament_forces.argtypes = [P, C.c_int32, P, P]
+        L.ora_set_morse.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.ora_morse_energy.restype = C.c_double
+        L.ora_morse_energy.argtypes = [P, P]
+        L.ora_morse_forces.argtypes = [P, P, P]
         _lib = L
     return _lib
 
@@ -131,6 +138,7 @@ def make_body(d) -> _Body:
     b.kind, b.first, b.count = int(d['kind']), int(d['first']), int(d['count'])
     for k in ('kBT_p', 'k_b', 'k_l', 'k_g', 'k_v', 'kappa', 'mass'):
         setattr(b, k, float(d[k]))
+    b.l0 = float(d.get('l0', 0.0))
     for k, n in (('inertia', 3), ('center', 3), ('quat', 4), ('vel', 3), ('omega', 3)):
         arr = getattr(b, k)
         for i in range(n):
@@ -172,6 +180,8 @@ class Oracle:
         if w.get('mesh') is not None:
             o.set_mesh(w['mesh']['tris'], w['mesh']['rest_X'])
         o.set_bodies(w.get('bodies', []), w['X'])
+        if w.get('morse') is not None:
+            o.set_morse(**w['morse'])
         return o
 
     # lattice
@@ -249,6 +259,27 @@ class Oracle:
         Xb = _f64(Xb)
         F = np.zeros_like(Xb)
         lib().ora_membrane_forces(self._h, b, _p(Xb), _p(F))
+        return F
+
+    def filament_energy(self, b, Xb):
+        return lib().ora_filament_energy(self._h, b, _p(_f64(Xb)))
+
+    def filament_forces(self, b, Xb):
+        Xb = _f64(Xb)
+        F = np.zeros_like(Xb)
+        lib().ora_filament_forces(self._h, b, _p(Xb), _p(F))
+        return F
+
+    def set_morse(self, D0, alpha, r0, rc):
+        lib().ora_set_morse(self._h, float(D0), float(alpha), float(r0), float(rc))
+
+    def morse_energy(self, X):
+        return lib().ora_morse_energy(self._h, _p(_f64(X)))
+
+    def morse_forces(self, X):
+        X = _f64(X)
+        F = np.zeros_like(X)
+        lib().ora_morse_forces(self._h, _p(X), _p(F))
         return F
 
     def mesh_rest(self):

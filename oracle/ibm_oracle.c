@@ -66,6 +66,8 @@ struct ora {
   edge_t* edges;
   double *l0, *th0, *At0;
   double A0, V0;
+  /* Morse excluded volume */
+  double morse_D0, morse_alpha, morse_r0, morse_rc;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -550,6 +552,7 @@ int ora_set_bodies(ora_t* o, int32_t nb, const ora_body* bodies, int64_t M, cons
     const ora_body* B = &o->bodies[b];
     if (B->first < 0 || B->count < 0 || B->first + B->count > M) return -1;
     if (B->kind == 0 && B->count != o->nv) return -2;
+    if (B->kind == 2 && (B->count < 2 || !(B->l0 > 0.0))) return -3;
     if (B->kind == 1) {
       double R[3][3];
       quat_matrix(B->quat, R);
@@ -620,6 +623,161 @@ static void rigid_forces(ora_t* o, ora_body* B) {
   for (int a = 0; a < 4; ++a) B->quat[a] /= n;
 }
 
+/* ------------------------------------------------------------------------ */
+/* filaments (Sec. 2.2, polymer particles)                                    */
+/* ------------------------------------------------------------------------ */
+/* Bond energy of Eq. inPlanePotential for one bond of length l, rest l0:
+ * WLC with x = l / l_m, l_m = 2 l0, plus the POW term k_p / l with
+ * k_p = 1.25 (kBT/p) l0^2 (zero bond force at l = l0). */
+static double bond_energy(double kBT_p, double l0, double l) {
+  const double lm = 2.0 * l0, x = l / lm, kp = 1.25 * kBT_p * l0 * l0;
+  return kBT_p * lm / 4.0 * (3.0 * x * x - 2.0 * x * x * x) / (1.0 - x) + kp / l;
+}
+static double bond_dUdl(double kBT_p, double l0, double l) {
+  const double x = l / (2.0 * l0), kp = 1.25 * kBT_p * l0 * l0;
+  return kBT_p * (0.25 / ((1.0 - x) * (1.0 - x)) - 0.25 + x) - kp / (l * l);
+}
+
+/* angle at bead j between the bonds to its neighbours, in [0, pi] */
+static double bead_angle(const double* a, const double* j, const double* c) {
+  double u[3], v[3], w[3];
+  sub3(a, j, u);
+  sub3(c, j, v);
+  cross3(u, v, w);
+  return atan2(norm3(w), dot3(u, v));
+}
+
+double ora_filament_energy(const ora_t* o, int32_t bi, const double* X) {
+  const ora_body* B = &o->bodies[bi];
+  const int64_t n = B->count;
+  double U = 0.0;
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    double p[3], q[3], d[3];
+    vget(X, n, j, p);
+    vget(X, n, j + 1, q);
+    sub3(q, p, d);
+    U += bond_energy(B->kBT_p, B->l0, norm3(d));
+  }
+  for (int64_t j = 1; j + 1 < n; ++j) {
+    double a[3], b[3], c[3];
+    vget(X, n, j - 1, a);
+    vget(X, n, j, b);
+    vget(X, n, j + 1, c);
+    const double dth = bead_angle(a, b, c) - M_PI;  /* theta0 = 180 degrees */
+    U += B->k_b * dth * dth;
+  }
+  return U;
+}
+
+void ora_filament_forces(const ora_t* o, int32_t bi, const double* X, double* F) {
+  const ora_body* B = &o->bodies[bi];
+  const int64_t n = B->count;
+  memset(F, 0, sizeof(double) * 3 * n);
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    double p[3], q[3], d[3];
+    vget(X, n, j, p);
+    vget(X, n, j + 1, q);
+    sub3(q, p, d);
+    const double l = norm3(d), s = bond_dUdl(B->kBT_p, B->l0, l) / l;
+    add3(F, n, j, d, s);    /* -dU/dp = dU/dl (q - p)/l */
+    add3(F, n, j + 1, d, -s);
+  }
+  for (int64_t j = 1; j + 1 < n; ++j) {
+    /* U = k_b (theta - pi)^2, cos(theta) = u.v / (|u||v|), u = a - b, v = c - b;
+     * dU/dcos = 2 k_b (pi - theta) / sin(theta), whose limit at theta = pi is 2 k_b */
+    double a[3], b[3], c[3], u[3], v[3], w[3];
+    vget(X, n, j - 1, a);
+    vget(X, n, j, b);
+    vget(X, n, j + 1, c);
+    sub3(a, b, u);
+    sub3(c, b, v);
+    cross3(u, v, w);
+    const double lu = norm3(u), lv = norm3(v);
+    const double sn = norm3(w) / (lu * lv), cs = dot3(u, v) / (lu * lv);
+    const double phi = M_PI - atan2(norm3(w), dot3(u, v));
+    const double ratio = sn > 1e-12 ? phi / sn : 1.0 + phi * phi / 6.0;
+    const double g = 2.0 * B->k_b * ratio;
+    double fa[3], fc[3];
+    for (int k = 0; k < 3; ++k) {
+      fa[k] = -g * (v[k] / (lu * lv) - cs * u[k] / (lu * lu));
+      fc[k] = -g * (u[k] / (lu * lv) - cs * v[k] / (lv * lv));
+    }
+    add3(F, n, j - 1, fa, 1.0);
+    add3(F, n, j + 1, fc, 1.0);
+    add3(F, n, j, fa, -1.0);
+    add3(F, n, j, fc, -1.0);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morse excluded volume between bodies (Eq. morsePotential)                  */
+/* ------------------------------------------------------------------------ */
+void ora_set_morse(ora_t* o, double D0, double alpha, double r0, double rc) {
+  o->morse_D0 = D0; o->morse_alpha = alpha; o->morse_r0 = r0; o->morse_rc = rc;
+}
+
+/* body of each marker taking part (membranes, filaments), -1 otherwise */
+static int32_t* morse_owner(const ora_t* o) {
+  int32_t* own = (int32_t*)malloc(sizeof(int32_t) * (o->M ? o->M : 1));
+  for (int64_t k = 0; k < o->M; ++k) own[k] = -1;
+  for (int b = 0; b < o->nb; ++b)
+    if (o->bodies[b].kind == 0 || o->bodies[b].kind == 2)
+      for (int64_t k = o->bodies[b].first; k < o->bodies[b].first + o->bodies[b].count; ++k) own[k] = b;
+  return own;
+}
+
+/* nearest-image separation X_k - X_j on the periodic axes of the geometry */
+static void separation(const ora_t* o, const double* X, int64_t k, int64_t j, double d[3]) {
+  const int64_t M = o->M;
+  const int n[3] = {o->cfg.nx, o->cfg.ny, o->cfg.nz};
+  const int periodic[3] = {1, o->cfg.geometry == 0, o->cfg.geometry != 2};
+  for (int a = 0; a < 3; ++a) {
+    d[a] = X[a * M + k] - X[a * M + j];
+    if (periodic[a]) d[a] -= n[a] * floor(d[a] / n[a] + 0.5);
+  }
+}
+
+double ora_morse_energy(const ora_t* o, const double* X) {
+  if (!(o->morse_rc > 0.0)) return 0.0;
+  int32_t* own = morse_owner(o);
+  double U = 0.0;
+  for (int64_t k = 0; k < o->M; ++k)
+    for (int64_t j = k + 1; j < o->M; ++j) {
+      if (own[k] < 0 || own[j] < 0 || own[k] == own[j]) continue;
+      double d[3];
+      separation(o, X, k, j, d);
+      const double r = norm3(d);
+      if (r >= o->morse_rc) continue;
+      const double e = exp(-o->morse_alpha * (r - o->morse_r0));
+      U += o->morse_D0 * (e * e - 2.0 * e);
+    }
+  free(own);
+  return U;
+}
+
+void ora_morse_forces(const ora_t* o, const double* X, double* F) {
+  const int64_t M = o->M;
+  memset(F, 0, sizeof(double) * 3 * (M ? M : 1));
+  if (!(o->morse_rc > 0.0)) return;
+  int32_t* own = morse_owner(o);
+  for (int64_t k = 0; k < M; ++k)
+    for (int64_t j = k + 1; j < M; ++j) {
+      if (own[k] < 0 || own[j] < 0 || own[k] == own[j]) continue;
+      double d[3];
+      separation(o, X, k, j, d);
+      const double r = norm3(d);
+      if (r >= o->morse_rc) continue;
+      /* dU/dr = 2 alpha D0 (e - e^2), e = exp(-alpha (r - r0)); F_k = -dU/dr d/r */
+      const double e = exp(-o->morse_alpha * (r - o->morse_r0));
+      const double s = -2.0 * o->morse_alpha * o->morse_D0 * (e - e * e) / r;
+      for (int a = 0; a < 3; ++a) {
+        F[a * M + k] += s * d[a];
+        F[a * M + j] -= s * d[a];
+      }
+    }
+  free(own);
+}
+
 void ora_stage_forces(ora_t* o) {
   int64_t M = o->M;
   memset(o->F, 0, sizeof(double) * 3 * (M ? M : 1));
@@ -635,7 +793,21 @@ void ora_stage_forces(ora_t* o) {
       ora_membrane_forces(o, b, Xb, Fb);
       for (int a = 0; a < 3; ++a) memcpy(o->F + a * M + B->first, Fb + a * nv, sizeof(double) * nv);
       free(Xb); free(Fb);
+    } else if (B->kind == 2) {
+      const int64_t n = B->count;
+      double* Xb = (double*)malloc(sizeof(double) * 3 * (n ? n : 1));
+      double* Fb = (double*)malloc(sizeof(double) * 3 * (n ? n : 1));
+      for (int a = 0; a < 3; ++a) memcpy(Xb + a * n, o->X + a * M + B->first, sizeof(double) * n);
+      ora_filament_forces(o, b, Xb, Fb);
+      for (int a = 0; a < 3; ++a) memcpy(o->F + a * M + B->first, Fb + a * n, sizeof(double) * n);
+      free(Xb); free(Fb);
     }
+  }
+  if (o->morse_rc > 0.0 && M > 0) {
+    double* Fm = (double*)malloc(sizeof(double) * 3 * M);
+    ora_morse_forces(o, o->X, Fm);
+    for (int64_t i = 0; i < 3 * M; ++i) o->F[i] += Fm[i];
+    free(Fm);
   }
 }
 

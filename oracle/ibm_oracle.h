@@ -35,7 +35,9 @@ typedef struct {
 } ora_config;
 
 typedef struct {
-  int32_t kind;         /* 0 membrane (Eq. membrane-potential), 1 rigid (penalty tether) */
+  int32_t kind;         /* 0 membrane (Eq. membrane-potential), 1 rigid (penalty tether),
+                           2 filament (bead chain: Eq. inPlanePotential bonds, Eq.
+                           bendingEnergyWorm angles) */
   int32_t pad;
   int64_t first, count; /* marker range */
   double kBT_p, k_b, k_l, k_g, k_v;   /* membrane moduli, lattice units */
@@ -43,6 +45,7 @@ typedef struct {
   double mass, inertia[3];             /* rigid: mass, principal moments (body frame) */
   double center[3], quat[4];           /* rigid: pose, quaternion (w,x,y,z) body->world */
   double vel[3], omega[3];             /* rigid: velocity, angular velocity (world) */
+  double l0;                           /* filament: rest bond length */
 } ora_body;
 
 typedef struct ora ora_t;
@@ -71,7 +74,7 @@ void ora_set_marker_forces(ora_t* o, const double* F);
 void ora_get_body(const ora_t* o, int32_t b, ora_body* out);
 
 /* The step, stage by stage, in this order. */
-void ora_stage_forces(ora_t* o);          /* marker forces (and rigid-body update) */
+void ora_stage_forces(ora_t* o);          /* marker forces (internal, then Morse; rigid-body update) */
 void ora_stage_spread(ora_t* o);          /* Eq. ibmForceSpread */
 void ora_stage_collide_stream(ora_t* o);  /* Eq. lbm with BGK and Guo forcing */
 void ora_stage_interpolate(ora_t* o);     /* Eq. ibmVelocityInterpret, then X += U */
@@ -86,6 +89,18 @@ void ora_guo(double tau, const double u[3], const double g[3], double F[19]);
  * bendingEnergy, areaEnergy, volumeEnergy), and its analytic forces -dU/dX. */
 double ora_membrane_energy(const ora_t* o, int32_t b, const double* X);
 void ora_membrane_forces(const ora_t* o, int32_t b, const double* X, double* F);
+/* Filament energy of one body at positions X [3][count] (bonds of Eq.
+ * inPlanePotential with l_m = 2 l0 and k_p = 1.25 (kBT/p) l0^2; angles of Eq.
+ * bendingEnergyWorm with theta0 = pi), and its analytic forces -dU/dX. */
+double ora_filament_energy(const ora_t* o, int32_t b, const double* X);
+void ora_filament_forces(const ora_t* o, int32_t b, const double* X, double* F);
+/* Morse excluded volume (Eq. morsePotential) between markers of different
+ * membrane or filament bodies, r < rc; rc <= 0 switches it off. Periodic
+ * axes use the nearest image. ora_morse_energy: total over all pairs at
+ * positions X [3][M]; ora_morse_forces: -dU/dX [3][M]. */
+void ora_set_morse(ora_t* o, double D0, double alpha, double r0, double rc);
+double ora_morse_energy(const ora_t* o, const double* X);
+void ora_morse_forces(const ora_t* o, const double* X, double* F);
 /* Rest-state quantities derived from the template: A0, V0, mean l0. */
 void ora_mesh_rest(const ora_t* o, double out[3]);
 /* Shear modulus of the WLC-POW network (Eq. shearModulus). */

@@ -24,6 +24,7 @@ import numpy as np
 # Body kinds understood by both sides.
 BODY_MEMBRANE = 0
 BODY_RIGID = 1
+BODY_FILAMENT = 2
 
 # Geometry codes.
 GEOM_PERIODIC = 0
@@ -163,6 +164,20 @@ def rbc_moduli_lattice(dx_m: float, tau: float):
                 k_v=2.2 / (u['force'] / dx_m ** 2))
 
 
+def filament_moduli_lattice(dx_m: float, tau: float, k_b_J: float = 4.1e-20):
+    """The paper's filament parameters (Table tab:paraPtlCellMix: kBT/p =
+    1.36e-12 N, bending k_b in [4.1e-20, 4.1e-18] J) in lattice units."""
+    u = lattice_units(dx_m, tau)
+    return dict(kBT_p=1.36e-12 / u['force'], k_b=k_b_J / u['energy'])
+
+
+def morse_lattice(dx_m: float, tau: float):
+    """The paper's Morse parameters (D0 = 1.2e-18 J, alpha = 0.5 per um,
+    r0 = rc = 0.66 um) in lattice units."""
+    u = lattice_units(dx_m, tau)
+    return dict(D0=1.2e-18 / u['energy'], alpha=0.5e6 * dx_m, r0=0.66e-6 / dx_m, rc=0.66e-6 / dx_m)
+
+
 # ----------------------------------------------------------------------------
 # bodies
 # ----------------------------------------------------------------------------
@@ -170,9 +185,18 @@ def _body(kind, first, count, **kw):
     b = dict(kind=kind, first=int(first), count=int(count),
              kBT_p=0.0, k_b=0.0, k_l=0.0, k_g=0.0, k_v=0.0, kappa=0.0, mass=0.0,
              inertia=[0.0, 0.0, 0.0], center=[0.0, 0.0, 0.0], quat=[1.0, 0.0, 0.0, 0.0],
-             vel=[0.0, 0.0, 0.0], omega=[0.0, 0.0, 0.0])
+             vel=[0.0, 0.0, 0.0], omega=[0.0, 0.0, 0.0], l0=0.0)
     b.update(kw)
     return b
+
+
+def filament(first, n_beads, start, direction, l0=1.0, kBT_p=0.0, k_b=0.0):
+    """A straight bead chain (its rest state: bonds of length l0, angles of
+    180 degrees) from `start` along `direction`."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    X = (np.asarray(start, dtype=np.float64)[:, None] + l0 * d[:, None] * np.arange(n_beads)[None, :]).copy()
+    return X, _body(BODY_FILAMENT, first, n_beads, kBT_p=kBT_p, k_b=k_b, l0=l0)
 
 
 def rigid_ellipsoid(center, axes, quat, first, freq=9, kappa=0.02):
