@@ -61,7 +61,7 @@ typedef enum {
 
 enum { IBM_LBM_STORE_F32 = 0, IBM_LBM_STORE_F16_DEV = 1, IBM_LBM_STORE_BF16_DEV = 2 };
 enum { IBM_LBM_GEOM_PERIODIC = 0, IBM_LBM_GEOM_YWALLS = 1, IBM_LBM_GEOM_TUBE = 2 };
-enum { IBM_LBM_BODY_MEMBRANE = 0, IBM_LBM_BODY_RIGID = 1 };
+enum { IBM_LBM_BODY_MEMBRANE = 0, IBM_LBM_BODY_RIGID = 1, IBM_LBM_BODY_FILAMENT = 2 };
 enum { IBM_LBM_STAGE_FORCES = 0, IBM_LBM_STAGE_SPREAD = 1, IBM_LBM_STAGE_COLLIDE = 2,
        IBM_LBM_STAGE_INTERP = 3 };
 
@@ -97,18 +97,25 @@ typedef struct {
  * bodies tether each marker to a body-fixed point (penalty reading of the
  * rigid coupling of Sec. 2.3, Eq. FSIRigid): force on the fluid
  * F_k = -kappa (X_k - X_k^ref), reaction on the body, explicit Newton-Euler
- * update of the pose. */
+ * update of the pose. Filaments (polymer particles of Sec. 2.2) are bead
+ * chains in marker order (count >= 2): each bond has the stretching energy
+ * of Eq. inPlanePotential with l_m = 2 l0 and k_p = 1.25 (kBT/p) l0^2 (no
+ * force at the rest length), each interior bead the bending energy
+ * k_b (theta - pi)^2 of Eq. bendingEnergyWorm (theta the angle between its
+ * two bonds; straight at rest). */
 typedef struct {
   int32_t kind;                 /* IBM_LBM_BODY_* */
   int32_t pad;
   int64_t first, count;         /* marker range */
   double kBT_p, k_b, k_l, k_g, k_v;  /* membrane: kBT/p, bending, local/global
                                         area, volume moduli (Eqs. inPlanePotential,
-                                        bendingEnergy, areaEnergy, volumeEnergy) */
+                                        bendingEnergy, areaEnergy, volumeEnergy);
+                                        filament: kBT/p and k_b */
   double kappa;                 /* rigid: tether stiffness */
   double mass, inertia[3];      /* rigid: mass and principal moments (body frame) */
   double center[3], quat[4];    /* rigid: centre, unit quaternion (w,x,y,z) body->world */
   double vel[3], omega[3];      /* rigid: velocity, angular velocity (world frame) */
+  double l0;                    /* filament: rest bond length (> 0) */
 } ibm_lbm_body;
 
 /* Membrane template (Sec. 2.2): closed, consistently outward-oriented
@@ -153,6 +160,15 @@ int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
  * template too large), E_NOMEM. */
 int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
                         const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
+
+/* Morse excluded volume (Eq. morsePotential, Sec. 2.2) between markers of
+ * different membrane or filament bodies: U = D0 (e^{-2 alpha (r - r0)} -
+ * 2 e^{-alpha (r - r0)}) for r < rc, added to the marker forces after the
+ * bodies' own forces. Periodic axes use the nearest image. Rigid-body
+ * markers and tracers do not take part. rc <= 0 switches it off (the
+ * default). May be called before or after set_markers. Errors: E_ARG
+ * (D0 < 0, alpha <= 0 with rc > 0), E_NOMEM. */
+int ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double rc);
 
 /* Advance n_steps coupled steps (order above) and wait for them; the last
  * step also writes the moments of every fluid cell and a FP64 conservation
@@ -226,9 +242,9 @@ typedef struct {
 } ibm_lbm_server_config;
 
 /* One case: lattice (storage must be IBM_LBM_STORE_F32), initial state
- * (rho0 [N] / u0 [3][N], either NULL for rest), markers, bodies, mesh (as
- * ibm_lbm_set_markers) and the number of steps to run. All host arrays are
- * copied at submission. */
+ * (rho0 [N] / u0 [3][N], either NULL for rest), markers, bodies (membranes,
+ * rigid bodies; no filaments), mesh (as ibm_lbm_set_markers) and the number
+ * of steps to run. All host arrays are copied at submission. */
 typedef struct {
   ibm_lbm_config lattice;
   const double* rho0;

@@ -43,7 +43,7 @@ class Body(C.Structure):
                 ('kBT_p', C.c_double), ('k_b', C.c_double), ('k_l', C.c_double), ('k_g', C.c_double),
                 ('k_v', C.c_double), ('kappa', C.c_double), ('mass', C.c_double),
                 ('inertia', C.c_double * 3), ('center', C.c_double * 3), ('quat', C.c_double * 4),
-                ('vel', C.c_double * 3), ('omega', C.c_double * 3)]
+                ('vel', C.c_double * 3), ('omega', C.c_double * 3), ('l0', C.c_double)]
 
 
 class Mesh(C.Structure):
@@ -91,6 +91,7 @@ def load():
         'ibm_lbm_set_populations': ([P, P], C.c_int),
         'ibm_lbm_get_populations': ([P, P], C.c_int),
         'ibm_lbm_set_markers': ([P, C.POINTER(Mesh), I32, P, I64, P], C.c_int),
+        'ibm_lbm_set_morse': ([P, D, D, D, D], C.c_int),
         'ibm_lbm_step': ([P, I64], C.c_int),
         'ibm_lbm_step_async': ([P, I64], C.c_int),
         'ibm_lbm_synchronize': ([P], C.c_int),
@@ -185,6 +186,10 @@ def ibm_lbm_set_markers(h, mesh: Mesh | None, bodies, X):
     arr = (Body * max(1, len(bodies)))(*bodies) if bodies else (Body * 1)()
     return _check(h, load().ibm_lbm_set_markers(h, C.byref(mesh) if mesh is not None else None,
                                                 len(bodies), arr, X.shape[1], _p(X)))
+
+
+def ibm_lbm_set_morse(h, D0, alpha, r0, rc):
+    return _check(h, load().ibm_lbm_set_morse(h, float(D0), float(alpha), float(r0), float(rc)))
 
 
 def ibm_lbm_step(h, n):
@@ -362,7 +367,7 @@ def make_config(lattice: dict, storage='f32', device=0) -> Config:
 def make_body(d) -> Body:
     b = Body()
     b.kind, b.first, b.count = int(d['kind']), int(d['first']), int(d['count'])
-    for k in ('kBT_p', 'k_b', 'k_l', 'k_g', 'k_v', 'kappa', 'mass'):
+    for k in ('kBT_p', 'k_b', 'k_l', 'k_g', 'k_v', 'kappa', 'mass', 'l0'):
         setattr(b, k, float(d.get(k, 0.0)))
     for k, n in (('inertia', 3), ('center', 3), ('quat', 4), ('vel', 3), ('omega', 3)):
         arr = getattr(b, k)
@@ -404,6 +409,8 @@ class Simulation:
     def from_workload(cls, w: dict, storage='f32', device=0, **kw):
         s = cls(w['lattice'], storage=storage, device=device, **kw)
         s.set_lattice(w.get('rho0'), w.get('u0'))
+        if w.get('morse') is not None:
+            s.set_morse(**w['morse'])
         s.set_markers(w.get('mesh'), w.get('bodies', []), w['X'])
         return s
 
@@ -443,6 +450,9 @@ class Simulation:
         ibm_lbm_set_markers(self.h, m, [make_body(b) for b in bodies], X)
         self.M = X.shape[1]
         self.n_bodies = len(bodies)
+
+    def set_morse(self, D0, alpha, r0, rc):
+        ibm_lbm_set_morse(self.h, D0, alpha, r0, rc)
 
     def set_marker_forces(self, F):
         ibm_lbm_set_marker_forces(self.h, F)

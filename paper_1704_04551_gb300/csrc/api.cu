@@ -80,14 +80,24 @@ LatticeDev lat(const ibm_lbm_t* h, bool odd) {
   return L;
 }
 
+// Marker forces: each body's own forces (membranes, rigid tethers,
+// filaments), then the Morse excluded volume between bodies.
+void enqueue_forces(ibm_lbm_t* h, cudaStream_t st) {
+  if (h->m.M == 0) return;
+  if (h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
+  launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
+  launch_filaments(h->m, h->d_bodies, h->filament_list, h->n_filaments, st);
+  if (h->morse_rc > 0.0 && h->morse_ready)
+    launch_morse(h->morse, h->m, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.geometry, st);
+}
+
 // One coupled step on the handle's stream (also used under capture).
 void enqueue_step(ibm_lbm_t* h, bool odd, bool dense) {
   cudaStream_t st = h->stream;
   const LatticeDev L = lat(h, odd);
   cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
   if (h->m.M > 0) {
-    if (h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
-    launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
+    enqueue_forces(h, st);
     launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   }
   launch_collide(L, h->rows, h->n_rows, h->cfg.storage, odd, dense, st);
@@ -104,9 +114,8 @@ void enqueue_timed_step(ibm_lbm_t* h, bool odd, bool dense) {
   };
   const LatticeDev L = lat(h, odd);
   cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st);
-  if (h->m.M > 0 && h->need_zero_F) cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st);
   mark(0);
-  if (h->m.M > 0) launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
+  enqueue_forces(h, st);
   mark(1);
   if (h->m.M > 0) launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
   mark(2);
@@ -365,6 +374,48 @@ std::vector<RowInfo> build_rows(const LatticeDev& L) {
   return rows;
 }
 
+// Cell-list buffers of the Morse interaction for the current markers:
+// bins at least rc wide on every axis, at most morse_max_bins() of them.
+int prepare_morse(ibm_lbm_t* h) {
+  release_pool(h, h->morse_mem);
+  h->morse_ready = false;
+  const int M = h->m.M;
+  const double rc = h->morse_rc;
+  const int n[3] = {h->cfg.nx, h->cfg.ny, h->cfg.nz};
+  int nb[3];
+  for (int a = 0; a < 3; ++a) nb[a] = std::max(1, (int)std::floor(n[a] / rc));
+  while ((long long)nb[0] * nb[1] * nb[2] > morse_max_bins()) {
+    const int a = nb[0] >= nb[1] && nb[0] >= nb[2] ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+    nb[a] = std::max(1, nb[a] / 2);
+  }
+  MorseDev& P = h->morse;
+  P = MorseDev{};
+  P.D0 = (float)h->morse_D0;
+  P.alpha = (float)h->morse_alpha;
+  P.r0 = (float)h->morse_r0;
+  P.rc2 = (float)(rc * rc);
+  for (int a = 0; a < 3; ++a) {
+    P.nb[a] = nb[a];
+    P.inv_bs[a] = (float)nb[a] / (float)n[a];
+  }
+  P.n_bins = nb[0] * nb[1] * nb[2];
+  P.owner = h->owner;
+  const size_t Mx = (size_t)std::max(M, 1);
+  P.count = (int*)dalloc(h, h->morse_mem, sizeof(int) * P.n_bins);
+  P.start = (int*)dalloc(h, h->morse_mem, sizeof(int) * ((size_t)P.n_bins + 1));
+  P.block_sum = (int*)dalloc(h, h->morse_mem, sizeof(int) * (size_t)morse_scan_tiles(P.n_bins));
+  P.bin_of = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
+  P.rank = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
+  P.sorted = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
+  P.sorted_id = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
+  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id)
+    return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  CUDA_TRY(h, cudaMemset(P.count, 0, sizeof(int) * P.n_bins));
+  CUDA_TRY(h, cudaMemset(P.start, 0, sizeof(int) * ((size_t)P.n_bins + 1)));
+  h->morse_ready = true;
+  return IBM_LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -464,6 +515,7 @@ int ibm_lbm_destroy(ibm_lbm_t* h) {
   for (auto e : h->events) cudaEventDestroy(e);
   h->events.clear();
   drop_graphs(h);
+  release_pool(h, h->morse_mem);
   release_pool(h, h->marker_mem);
   release_pool(h, h->lattice_mem);
   if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -545,8 +597,13 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     return fail(h, IBM_LBM_E_ARG, "set_markers: bad counts or null arrays");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   drop_graphs(h);
+  release_pool(h, h->morse_mem);
   release_pool(h, h->marker_mem);
   h->m = MarkersDev{};
+  h->morse_ready = false;
+  h->owner = nullptr;
+  h->filament_list = nullptr;
+  h->n_filaments = 0;
   h->n_bodies = 0;
   h->d_bodies = nullptr;
   h->h_bodies.clear();
@@ -574,6 +631,9 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
       any_rigid = true;
       if (!(B.mass > 0) || !(B.inertia[0] > 0) || !(B.inertia[1] > 0) || !(B.inertia[2] > 0) || !(B.kappa >= 0))
         return fail(h, IBM_LBM_E_ARG, "set_markers: rigid body needs mass, inertia > 0 and kappa >= 0");
+    } else if (B.kind == IBM_LBM_BODY_FILAMENT) {
+      if (B.count < 2 || !(B.l0 > 0) || !(B.kBT_p >= 0) || !(B.k_b >= 0))
+        return fail(h, IBM_LBM_E_ARG, "set_markers: filament needs >= 2 beads, l0 > 0, kBT_p >= 0 and k_b >= 0");
     } else {
       return fail(h, IBM_LBM_E_ARG, "set_markers: unknown body kind");
     }
@@ -631,6 +691,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     D.count = (int)B.count;
     D.kBT_p = (float)B.kBT_p; D.k_b = (float)B.k_b; D.k_l = (float)B.k_l; D.k_g = (float)B.k_g; D.k_v = (float)B.k_v;
     D.kappa = B.kappa; D.mass = B.mass;
+    D.l0 = (float)B.l0;
     for (int a = 0; a < 3; ++a) {
       D.inertia[a] = B.inertia[a]; D.center[a] = B.center[a]; D.vel[a] = B.vel[a]; D.omega[a] = B.omega[a];
     }
@@ -640,12 +701,21 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   if ((rc = upload<BodyDev>(h, h->marker_mem, &h->d_bodies, bd.data(), bd.size()))) return rc;
   h->n_bodies = n_bodies;
   {
-    std::vector<int> mem, rig;
-    for (int b = 0; b < n_bodies; ++b) (bodies[b].kind == IBM_LBM_BODY_MEMBRANE ? mem : rig).push_back(b);
+    std::vector<int> mem, rig, fil;
+    std::vector<int> own((size_t)std::max(M, 1), -1);
+    for (int b = 0; b < n_bodies; ++b) {
+      const int kind = bodies[b].kind;
+      (kind == IBM_LBM_BODY_MEMBRANE ? mem : kind == IBM_LBM_BODY_RIGID ? rig : fil).push_back(b);
+      if (kind != IBM_LBM_BODY_RIGID)
+        for (int64_t k = bodies[b].first; k < bodies[b].first + bodies[b].count; ++k) own[k] = b;
+    }
     h->n_membranes = (int)mem.size();
     h->n_rigids = (int)rig.size();
+    h->n_filaments = (int)fil.size();
     if ((rc = upload<int>(h, h->marker_mem, &h->membrane_list, mem.data(), mem.size()))) return rc;
     if ((rc = upload<int>(h, h->marker_mem, &h->rigid_list, rig.data(), rig.size()))) return rc;
+    if ((rc = upload<int>(h, h->marker_mem, &h->filament_list, fil.data(), fil.size()))) return rc;
+    if ((rc = upload<int>(h, h->marker_mem, &h->owner, own.data(), own.size()))) return rc;
   }
   // mesh
   if (any_membrane) {
@@ -719,6 +789,23 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     if (!h->boxes) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
   }
   h->need_zero_F = covered < n_markers;
+  if (h->morse_rc > 0.0) return prepare_morse(h);
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double rc) {
+  if (!h) return IBM_LBM_E_ARG;
+  if (rc > 0.0 && (!(D0 >= 0.0) || !(alpha > 0.0) || !std::isfinite(r0) || !std::isfinite(rc)))
+    return fail(h, IBM_LBM_E_ARG, "set_morse: needs D0 >= 0, alpha > 0 and finite r0, rc");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  h->morse_D0 = D0;
+  h->morse_alpha = alpha;
+  h->morse_r0 = r0;
+  h->morse_rc = rc > 0.0 ? rc : 0.0;
+  release_pool(h, h->morse_mem);
+  h->morse_ready = false;
+  if (h->morse_rc > 0.0 && h->owner) return prepare_morse(h);
   return IBM_LBM_OK;
 }
 
@@ -744,10 +831,7 @@ int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
   cudaStream_t st = h->stream;
   switch (stage) {
     case IBM_LBM_STAGE_FORCES:
-      if (h->m.M > 0) {
-        if (h->need_zero_F) CUDA_TRY(h, cudaMemsetAsync(h->m.F, 0, sizeof(float4) * (size_t)h->m.M, st));
-        launch_forces(h->m, h->d_bodies, h->membrane_list, h->n_membranes, h->rigid_list, h->n_rigids, h->mesh, st);
-      }
+      enqueue_forces(h, st);
       break;
     case IBM_LBM_STAGE_SPREAD: {
       const LatticeDev L = lat(h, h->odd_next);

@@ -133,6 +133,23 @@ struct BodyDev {
   double kappa, mass, inertia[3];
   double center[3], quat[4], vel[3], omega[3];
   float qmax;  // membranes: largest force contribution component of the last step (0: none yet)
+  float l0;    // filaments: rest bond length
+};
+
+// Morse excluded volume between bodies: a cell list rebuilt every step.
+struct MorseDev {
+  float D0, alpha, r0, rc2;
+  int nb[3];          // bins per axis
+  float inv_bs[3];    // 1 / bin size
+  int n_bins;
+  int* count;         // [n_bins] markers per bin (zero between steps)
+  int* start;         // [n_bins + 1] exclusive prefix of count
+  int* block_sum;     // [scan blocks]
+  int* bin_of;        // [M]
+  int* rank;          // [M] position within the bin
+  float4* sorted;     // [M] wrapped position, owner body (int bits in w), by bin
+  int* sorted_id;     // [M] marker of each sorted slot
+  const int* owner;   // [M] body of a participating marker, -1 otherwise
 };
 
 struct MeshDev {

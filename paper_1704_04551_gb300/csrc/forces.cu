@@ -1,5 +1,5 @@
-// Marker-force kernels of one lattice: membranes (Sec. 2.2) one block per
-// body, rigid bodies (Sec. 2.3) one block per body; the bodies and their
+// Marker-force kernels of one lattice: membranes and filaments (Sec. 2.2)
+// and rigid bodies (Sec. 2.3), one block per body; the bodies and their
 // design notes are in forces_body.cuh.
 #include "common.cuh"
 #include "forces_body.cuh"
@@ -18,6 +18,15 @@ __global__ void __launch_bounds__(RIGID_THREADS) k_rigid(MarkersDev m, BodyDev* 
                                                          const int* __restrict__ list) {
   __shared__ double sh[6 * 32];
   rigid_block(m, bodies + list[blockIdx.x], sh);
+}
+
+__global__ void __launch_bounds__(FILAMENT_THREADS) k_filaments(MarkersDev m, const BodyDev* __restrict__ bodies,
+                                                                 const int* __restrict__ list) {
+  filament_block(m, bodies[list[blockIdx.x]]);
+}
+
+void launch_filaments(const MarkersDev& m, const BodyDev* bodies, const int* list, int n, cudaStream_t st) {
+  if (n > 0) k_filaments<<<n, FILAMENT_THREADS, 0, st>>>(m, bodies, list);
 }
 
 size_t membrane_work_floats(int nv, int nt, int ne) {

@@ -43,8 +43,10 @@ namespace forces_detail {
 
 constexpr int RIGID_THREADS = 256;
 constexpr int MEMBRANE_THREADS = 256;
+constexpr int FILAMENT_THREADS = 64;
 
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 cross(float3 a, float3 b) {
@@ -247,6 +249,84 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   if (threadIdx.x == 0) {
     const float q = __uint_as_float(s_qmax);
     Bp->qmax = isfinite(q) ? q : 0.f;
+  }
+}
+
+// Filament forces of one bead chain (polymer particles, Sec. 2.2) by the
+// whole thread block, one thread per bead: every bead gathers the terms
+// that involve it (its two bonds, the angle at itself and at each
+// neighbour), so no bead is written twice and no atomics are needed.
+//   bond (Eq. inPlanePotential): l_m = 2 l0, k_p = 1.25 (kBT/p) l0^2;
+//   angle (Eq. bendingEnergyWorm): U = k_b (theta - pi)^2, theta the angle
+//   between the two bonds at an interior bead; with cos(theta) = u.v/(|u||v|),
+//   u, v the bonds to the previous and next bead,
+//   dU/dcos = 2 k_b phi / sin(phi), phi = pi - theta (limit 2 k_b when straight),
+//   F_prev = -dU/dcos dcos/du, F_next = -dU/dcos dcos/dv, F_mid = -(F_prev + F_next).
+namespace forces_detail {
+
+// X_a - X_b from the stencil cache: exact integer part, one FP32 rounding
+__device__ __forceinline__ float3 marker_diff(const MarkersDev& m, int a, int b) {
+  const size_t M = (size_t)m.M;
+  return make_float3((float)(m.cell[a] - m.cell[b]) + (m.frac[a] - m.frac[b]),
+                     (float)(m.cell[M + a] - m.cell[M + b]) + (m.frac[M + a] - m.frac[M + b]),
+                     (float)(m.cell[2 * M + a] - m.cell[2 * M + b]) + (m.frac[2 * M + a] - m.frac[2 * M + b]));
+}
+
+// d cos(theta) / du and / dv for bonds u, v of one angle, and dU/dcos
+struct AngleGrad {
+  float3 du, dv;
+  float g;
+};
+__device__ __forceinline__ AngleGrad angle_grad(float3 u, float3 v, float k_b) {
+  const float lu = sqrtf(dot(u, u)), lv = sqrtf(dot(v, v));
+  const float3 w = cross(u, v);
+  const float sw = sqrtf(dot(w, w)), c = dot(u, v);
+  const float inv = 1.0f / (lu * lv), cs = c * inv, sn = sw * inv;
+  const float phi = atan2f(sw, -c);  // pi - theta
+  const float ratio = sn > 1e-6f ? phi / sn : 1.0f + phi * phi * (1.0f / 6.0f);
+  AngleGrad G;
+  G.g = 2.0f * k_b * ratio;
+  G.du = inv * v + (-cs / (lu * lu)) * u;
+  G.dv = inv * u + (-cs / (lv * lv)) * v;
+  return G;
+}
+
+}  // namespace forces_detail
+
+__device__ __forceinline__ void filament_block(const MarkersDev& m, const BodyDev& B) {
+  const int n = B.count, f = B.first;
+  const float l0 = B.l0, kBT_p = B.kBT_p, k_b = B.k_b;
+  const float kp = 1.25f * kBT_p * l0 * l0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    // bonds j-1 -> j and j -> j+1: F_j += dU/dl (X_other - X_j)/l
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+      const int o = j + side;
+      if (o < 0 || o >= n) continue;
+      const float3 e = marker_diff(m, f + o, f + j);
+      const float L2 = dot(e, e), l = sqrtf(L2), x = l / (2.0f * l0);
+      const float dUdl = kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
+      F = F + (dUdl / l) * e;
+    }
+    if (k_b != 0.f) {
+      // angle at j itself
+      if (j >= 1 && j + 1 < n) {
+        const AngleGrad G = angle_grad(marker_diff(m, f + j - 1, f + j), marker_diff(m, f + j + 1, f + j), k_b);
+        F = F + G.g * (G.du + G.dv);
+      }
+      // angle at j - 1: j is its next bead
+      if (j >= 2) {
+        const AngleGrad G = angle_grad(marker_diff(m, f + j - 2, f + j - 1), marker_diff(m, f + j, f + j - 1), k_b);
+        F = F + (-G.g) * G.dv;
+      }
+      // angle at j + 1: j is its previous bead
+      if (j + 2 < n) {
+        const AngleGrad G = angle_grad(marker_diff(m, f + j, f + j + 1), marker_diff(m, f + j + 2, f + j + 1), k_b);
+        F = F + (-G.g) * G.du;
+      }
+    }
+    m.F[f + j] = make_float4(F.x, F.y, F.z, 0.f);
   }
 }
 

@@ -47,9 +47,16 @@ struct ibm_lbm {
   BodyDev* d_bodies = nullptr;
   std::vector<ibm_lbm_body> h_bodies;
   MeshDev mesh{};
-  int* membrane_list = nullptr;   // body indices of membranes / rigid bodies
+  int* membrane_list = nullptr;   // body indices of membranes / rigid bodies / filaments
   int* rigid_list = nullptr;
-  int n_membranes = 0, n_rigids = 0;
+  int* filament_list = nullptr;
+  int n_membranes = 0, n_rigids = 0, n_filaments = 0;
+  int* owner = nullptr;           // [M] body of each membrane / filament marker, -1 otherwise
+  // Morse excluded volume (off while rc <= 0)
+  double morse_D0 = 0.0, morse_alpha = 0.0, morse_r0 = 0.0, morse_rc = 0.0;
+  ibm::MorseDev morse{};
+  bool morse_ready = false;       // cell-list buffers match the markers
+  std::vector<Alloc> morse_mem;
   int n_sm = 0;
   MarkerGroup* groups = nullptr;  // transfer blocks
   int n_groups = 0;

@@ -28,5 +28,11 @@ void launch_forces(const MarkersDev& m, BodyDev* bodies, const int* membranes, i
                    int n_rigids, const MeshDev& mesh, cudaStream_t st);
 size_t membrane_work_floats(int nv, int nt, int ne);
 cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem);
+void launch_filaments(const MarkersDev& m, const BodyDev* bodies, const int* list, int n, cudaStream_t st);
+
+// morse.cu
+void launch_morse(const MorseDev& P, const MarkersDev& m, int nx, int ny, int nz, int geometry, cudaStream_t st);
+int morse_scan_tiles(int n_bins);
+int morse_max_bins();
 
 }  // namespace ibm

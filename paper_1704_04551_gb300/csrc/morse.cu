@@ -1,0 +1,234 @@
+// Morse excluded volume between immersed bodies (Eq. morsePotential of
+// arXiv:1704.04551, Sec. 2.2):
+//   U = D0 (e^{-2 alpha (r - r0)} - 2 e^{-alpha (r - r0)}),  r < rc,
+// between markers of different membrane or filament bodies; the force on a
+// marker is F = -dU/dr d/r = 2 alpha D0 (e^2 - e) d/r, e = e^{-alpha (r - r0)},
+// d its separation from the other marker (nearest image on periodic axes).
+//
+// A cell list rebuilt every step: bins at least rc wide (at most 2^24 of
+// them), markers counted into bins with atomics, an exclusive prefix sum of
+// the counts, markers scattered into bin order (wrapped position and owner
+// body packed in a float4), then one thread per sorted marker gathers the
+// forces of the markers in the 27 bins around its own and adds them to its
+// marker force. Positions come from the stencil cache (floor + FP32
+// fraction), wrapped into the box on periodic axes, so separations are
+// exact to FP32 rounding of a coordinate below the box size.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibm {
+
+namespace {
+
+constexpr int MORSE_THREADS = 256;
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;  // per thread
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+struct Box {
+  int n[3];
+  int periodic[3];
+};
+
+__device__ __forceinline__ float wrapped_coord(const MarkersDev& m, const Box& B, int a, int k) {
+  const size_t M = (size_t)m.M;
+  int c = m.cell[a * M + k];
+  if (B.periodic[a]) c = wrapi(c, B.n[a]);
+  return (float)c + m.frac[a * M + k];
+}
+
+__device__ __forceinline__ int bin_coord(const MorseDev& P, int a, float x) {
+  const int b = (int)floorf(x * P.inv_bs[a]);
+  return min(max(b, 0), P.nb[a] - 1);
+}
+
+__global__ void k_morse_count(MorseDev P, MarkersDev m, Box B) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.M || P.owner[k] < 0) return;
+  int b[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) b[a] = bin_coord(P, a, wrapped_coord(m, B, a, k));
+  const int bin = b[0] + P.nb[0] * (b[1] + P.nb[1] * b[2]);
+  P.bin_of[k] = bin;
+  P.rank[k] = atomicAdd(P.count + bin, 1);
+}
+
+// exclusive scan of SCAN_ITEMS values per thread across the block; returns
+// this thread's exclusive prefix and the block total
+__device__ __forceinline__ int block_exclusive(int v, int& total) {
+  __shared__ int warp_tot[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;  // inclusive prefix of the warp totals
+  }
+  __syncthreads();
+  total = warp_tot[(blockDim.x >> 5) - 1];
+  const int before = warp == 0 ? 0 : warp_tot[warp - 1];
+  __syncthreads();  // warp_tot is reused by the next call
+  return before + x - v;
+}
+
+// tile-local exclusive prefix into start[], tile totals into block_sum[]
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(MorseDev P) {
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    v[i] = base + i < P.n_bins ? P.count[base + i] : 0;
+    s += v[i];
+  }
+  int total;
+  int run = block_exclusive(s, total);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (base + i < P.n_bins) P.start[base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 0) P.block_sum[blockIdx.x] = total;
+}
+
+// exclusive scan of the tile totals (one block); start[n_bins] = total
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_totals(MorseDev P, int n_tiles) {
+  const int base = threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    v[i] = base + i < n_tiles ? P.block_sum[base + i] : 0;
+    s += v[i];
+  }
+  int total;
+  int run = block_exclusive(s, total);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (base + i < n_tiles) P.block_sum[base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 0) P.start[P.n_bins] = total;
+}
+
+// add the tile offsets; clear the counts for the next step
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(MorseDev P) {
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  const int off = P.block_sum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i)
+    if (base + i < P.n_bins) {
+      P.start[base + i] += off;
+      P.count[base + i] = 0;
+    }
+}
+
+__global__ void k_morse_scatter(MorseDev P, MarkersDev m, Box B) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.M || P.owner[k] < 0) return;
+  const int slot = P.start[P.bin_of[k]] + P.rank[k];
+  P.sorted[slot] = make_float4(wrapped_coord(m, B, 0, k), wrapped_coord(m, B, 1, k), wrapped_coord(m, B, 2, k),
+                               __int_as_float(P.owner[k]));
+  P.sorted_id[slot] = k;
+}
+
+// Neighbour bins along one axis: first .. first + cnt - 1, taken modulo nb
+// on periodic axes (-1, 0, +1, or all bins when there are fewer than
+// three), clipped to the axis otherwise.
+struct AxisRange {
+  int first, cnt;
+};
+__device__ __forceinline__ AxisRange axis_range(int b, int nb, bool periodic) {
+  AxisRange r;
+  if (periodic) {
+    if (nb < 3) {
+      r.first = 0;
+      r.cnt = nb;
+    } else {
+      r.first = b - 1 + nb;  // kept non-negative for the modulo
+      r.cnt = 3;
+    }
+  } else {
+    r.first = max(b - 1, 0);
+    r.cnt = min(b + 1, nb - 1) - r.first + 1;
+  }
+  return r;
+}
+__device__ __forceinline__ int range_bin(const AxisRange& r, int d, int nb) {
+  const int v = r.first + d;
+  return v >= nb ? v % nb : v;
+}
+
+__global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, MarkersDev m, Box B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.start[P.n_bins]) return;
+  const float4 p = P.sorted[s];
+  const int own = __float_as_int(p.w);
+  const float pc[3] = {p.x, p.y, p.z};
+  const AxisRange rx = axis_range(bin_coord(P, 0, pc[0]), P.nb[0], B.periodic[0] != 0);
+  const AxisRange ry = axis_range(bin_coord(P, 1, pc[1]), P.nb[1], B.periodic[1] != 0);
+  const AxisRange rz = axis_range(bin_coord(P, 2, pc[2]), P.nb[2], B.periodic[2] != 0);
+  const float hx = 0.5f * B.n[0], hy = 0.5f * B.n[1], hz = 0.5f * B.n[2];
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (int iz = 0; iz < rz.cnt; ++iz)
+    for (int iy = 0; iy < ry.cnt; ++iy)
+      for (int ix = 0; ix < rx.cnt; ++ix) {
+        const int bin = range_bin(rx, ix, P.nb[0]) + P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
+        const int j1 = P.start[bin + 1];
+        for (int j = P.start[bin]; j < j1; ++j) {
+          const float4 q = P.sorted[j];
+          if (__float_as_int(q.w) == own) continue;
+          float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+          if (B.periodic[0]) dx = dx > hx ? dx - B.n[0] : (dx < -hx ? dx + B.n[0] : dx);
+          if (B.periodic[1]) dy = dy > hy ? dy - B.n[1] : (dy < -hy ? dy + B.n[1] : dy);
+          if (B.periodic[2]) dz = dz > hz ? dz - B.n[2] : (dz < -hz ? dz + B.n[2] : dz);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 < P.rc2) || r2 == 0.f) continue;
+          const float r = sqrtf(r2);
+          const float e = expf(-P.alpha * (r - P.r0));
+          const float c = 2.0f * P.alpha * P.D0 * (e * e - e) / r;
+          fx = fmaf(c, dx, fx);
+          fy = fmaf(c, dy, fy);
+          fz = fmaf(c, dz, fz);
+        }
+      }
+  const int k = P.sorted_id[s];
+  float4 F = m.F[k];
+  F.x += fx;
+  F.y += fy;
+  F.z += fz;
+  m.F[k] = F;
+}
+
+}  // namespace
+
+int morse_scan_tiles(int n_bins) { return (n_bins + SCAN_TILE - 1) / SCAN_TILE; }
+int morse_max_bins() { return SCAN_TILE * SCAN_TILE; }
+
+void launch_morse(const MorseDev& P, const MarkersDev& m, int nx, int ny, int nz, int geometry, cudaStream_t st) {
+  if (m.M == 0 || !(P.rc2 > 0.f)) return;
+  Box B;
+  B.n[0] = nx; B.n[1] = ny; B.n[2] = nz;
+  B.periodic[0] = 1;
+  B.periodic[1] = geometry == GEOM_PERIODIC;
+  B.periodic[2] = geometry != GEOM_TUBE;
+  const int grid = (m.M + MORSE_THREADS - 1) / MORSE_THREADS;
+  const int tiles = morse_scan_tiles(P.n_bins);
+  k_morse_count<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
+  k_scan_tiles<<<tiles, SCAN_THREADS, 0, st>>>(P);
+  k_scan_totals<<<1, SCAN_THREADS, 0, st>>>(P, tiles);
+  k_scan_add<<<tiles, SCAN_THREADS, 0, st>>>(P);
+  k_morse_scatter<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
+  k_morse_force<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
+}
+
+}  // namespace ibm

@@ -529,7 +529,11 @@ int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t*
   if (M) c->X.assign(in->X, in->X + 3 * M);
   if (in->n_bodies) c->bodies.assign(in->bodies, in->bodies + in->n_bodies);
   bool rigid = false;
-  for (auto& b : c->bodies) rigid |= b.kind == IBM_LBM_BODY_RIGID;
+  for (auto& b : c->bodies) {
+    rigid |= b.kind == IBM_LBM_BODY_RIGID;
+    if (b.kind != IBM_LBM_BODY_RIGID && b.kind != IBM_LBM_BODY_MEMBRANE)
+      return sfail(s, IBM_LBM_E_ARG, "submit: served cases hold membranes, rigid bodies and tracers");
+  }
   if (in->mesh) {
     if (!in->mesh->tris || !in->mesh->rest_X || in->mesh->n_vertices < 4 || in->mesh->n_triangles < 4)
       return sfail(s, IBM_LBM_E_ARG, "submit: invalid mesh");

@@ -352,6 +352,139 @@ def place_cells_in_tube(rng, n, radius, n_cells, diameter, max_tilt_deg=40.0, tr
     return centers, quats
 
 
+def place_cells_in_channel(rng, shape, x_range, n_cells, diameter, max_tilt_deg=40.0, tries=5):
+    """Seeded non-overlapping placement of red cells in a channel (walls at
+    y = -1/2 and ny - 1/2, periodic x and z) within x_range, the same scheme
+    as place_cells_in_tube: stacks of slots on a hexagonal grid of the
+    cross-section (spacing D + 2) filled at random with cells whose axis lies
+    along x, then a random spin, tilt (up to max_tilt_deg) and jitter kept
+    only where the cell's inflated bounding spheroid stays clear."""
+    nx, ny, nz = shape
+    a = 0.5 * diameter + 0.5
+    cz = 0.33 * 0.5 * diameter + 0.5
+    occ = np.zeros((nx, ny, nz), dtype=bool)
+    sp = diameter + 2.0
+    cols = []
+    for j in range(int(nz / (sp * math.sqrt(3.0) / 2.0)) + 1):
+        z = a + 0.5 + sp * j * math.sqrt(3.0) / 2.0
+        for i in range(int(ny / sp) + 1):
+            y = a + 0.5 + sp * (i + 0.5 * (j % 2))
+            if y <= ny - 1.5 - a and z <= nz - 1.5 - a:
+                cols.append((y, z))
+    x0, x1 = x_range
+    per_col = max(1, int((x1 - x0) // (2.0 * cz + 0.25)))
+    dxs = (x1 - x0) / per_col
+    slots = [(x0 + (k + 0.5) * dxs, y, z) for (y, z) in cols for k in range(per_col)]
+    if len(slots) < n_cells:
+        raise RuntimeError(f'only {len(slots)} slots for {n_cells} cells')
+    pick = sorted(rng.permutation(len(slots))[:n_cells])
+    ext = int(math.ceil(a)) + 1
+    off = np.arange(-ext, ext + 1)
+    ox, oy, oz = np.meshgrid(off, off, off, indexing='ij')
+    pts = np.stack([ox.ravel(), oy.ravel(), oz.ravel()], axis=1).astype(np.float64)
+    q_align = np.array([math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0])  # body z -> world x
+
+    def footprint(c, q):
+        R = quat_to_matrix(q)
+        p = pts + np.floor(c)
+        d = (p - c) @ R
+        inside = (d[:, 0] ** 2 + d[:, 1] ** 2) / (a * a) + d[:, 2] ** 2 / (cz * cz) <= 1.0
+        idx = p[inside].astype(np.int64)
+        if idx[:, 1].min() < 0 or idx[:, 1].max() >= ny or idx[:, 0].min() < x0 - 1 or idx[:, 0].max() > x1:
+            return None
+        return idx[:, 0] % nx, idx[:, 1], idx[:, 2] % nz
+
+    centers, quats, feet = [], [], []
+    for s_id in pick:
+        xs, y0, z0 = slots[s_id]
+        spin = 2 * math.pi * rng.random()
+        q = _qmul(q_align, np.array([math.cos(spin / 2), 0.0, 0.0, math.sin(spin / 2)]))
+        c = np.array([xs, y0, z0])
+        fp = footprint(c, q)
+        if fp is None or occ[fp].any():
+            raise RuntimeError('stack slot overlaps')
+        occ[fp] = True
+        centers.append(c)
+        quats.append(q)
+        feet.append(fp)
+    for k in rng.permutation(len(centers)):
+        occ[feet[k]] = False
+        tilt = math.radians(max_tilt_deg) * math.sqrt(rng.random())
+        azim = 2 * math.pi * rng.random()
+        jit = (rng.random(3) - 0.5) * np.array([0.5, 1.0, 1.0])
+        for t in range(tries):
+            tl = tilt * (0.5 ** t)
+            ax = np.array([0.0, math.cos(azim), math.sin(azim)])
+            q_tilt = np.concatenate([[math.cos(tl / 2)], math.sin(tl / 2) * np.cross([1.0, 0.0, 0.0], ax)])
+            q = _qmul(q_tilt, quats[k])
+            q /= np.linalg.norm(q)
+            c = centers[k] + jit
+            fp = footprint(c, q)
+            if fp is not None and not occ[fp].any():
+                centers[k], quats[k], feet[k] = c, q, fp
+                break
+        occ[feet[k]] = True
+    quats = [q if q[0] >= 0 else -q for q in quats]
+    return centers, quats
+
+
+def mixed_suspension(shape=(512, 512, 512), n_cells=20000, n_filaments=4000, beads=50, diameter=16.0,
+                     tau=1.0, wall_shear_rate=1000.0, seed=1709, dx_m=0.5e-6, jitter=0.2, freq=8,
+                     filament_spacing=3.0, steps=1000, morse=True):
+    """Red cells and flexible filaments in a channel (walls at rest at
+    y = -1/2 and ny - 1/2, periodic x and z), driven by a uniform body force
+    whose plane-Poiseuille wall shear rate is `wall_shear_rate` (1/s).
+    Filaments (bond length 1 lu, the lattice spacing) lie straight along x
+    in a slab at the channel inlet, on a jittered grid of the
+    cross-section, half with bending stiffness 10 kBT and half 1000 kBT
+    (4.1e-20 and 4.1e-18 J); cells fill the rest of the channel. Markers:
+    cells first, then filaments; Morse excluded volume between bodies."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    u = lattice_units(dx_m, tau)
+    nu = (tau - 0.5) / 3.0
+    g0 = 2.0 * nu * (wall_shear_rate * u['dt']) / ny
+    rest, tris = rbc_rest_shape(diameter, freq)
+    mod = rbc_moduli_lattice(dx_m, tau)
+    slab = beads + 2.0
+    centers, quats = place_cells_in_channel(rng, shape, (slab + 1.0, nx - 1.0), n_cells, diameter)
+    V = rest.shape[1]
+    M = V * len(centers) + beads * n_filaments
+    X = np.empty((3, M))
+    bodies = []
+    for k, (c, q) in enumerate(zip(centers, quats)):
+        R = quat_to_matrix(q)
+        X[:, k * V:(k + 1) * V] = (R @ rest) + c[:, None]
+        s = 1.0 + jitter * (2.0 * rng.random(5) - 1.0)
+        bodies.append(_body(BODY_MEMBRANE, k * V, V, kBT_p=mod['kBT_p'] * s[0], k_b=mod['k_b'] * s[1],
+                            k_l=mod['k_l'] * s[2], k_g=mod['k_g'] * s[3], k_v=mod['k_v'] * s[4],
+                            center=list(map(float, c)), quat=list(map(float, q))))
+    # filament grid on the cross-section, away from the walls
+    gy = np.arange(1.5, ny - 1.5, filament_spacing)
+    gz = np.arange(0.5, nz - 0.5, filament_spacing)
+    grid = np.array([(y, z) for z in gz for y in gy])
+    if len(grid) < n_filaments:
+        raise RuntimeError(f'only {len(grid)} filament sites for {n_filaments} filaments')
+    sites = grid[np.sort(rng.permutation(len(grid))[:n_filaments])]
+    soft = filament_moduli_lattice(dx_m, tau, 4.1e-20)
+    stiff = filament_moduli_lattice(dx_m, tau, 4.1e-18)
+    first = V * len(centers)
+    for f, (y, z) in enumerate(sites):
+        mod_f = soft if f % 2 == 0 else stiff
+        start = [1.0 + 0.5 * rng.random(), y + 0.4 * (rng.random() - 0.5), z + 0.4 * (rng.random() - 0.5)]
+        Xf, bf = filament(first, beads, start, [1.0, 0.0, 0.0], l0=1.0, kBT_p=mod_f['kBT_p'], k_b=mod_f['k_b'])
+        X[:, first:first + beads] = Xf
+        bodies.append(bf)
+        first += beads
+    lattice = dict(nx=nx, ny=ny, nz=nz, tau=tau, geometry=GEOM_YWALLS, wall_u=[0.0, 0.0],
+                   tube_radius=0.0, body_force=[g0, 0.0, 0.0])
+    w = dict(name=f'mixed_channel_{nx}x{ny}x{nz}_{len(centers)}cells_{n_filaments}x{beads}filaments',
+             lattice=lattice, mesh=dict(rest_X=rest, tris=tris), bodies=bodies, X=X, steps=steps, seed=seed)
+    if morse:
+        w['morse'] = morse_lattice(dx_m, tau)
+    return w
+
+
 def _qmul(p, q):
     w1, x1, y1, z1 = p
     w2, x2, y2, z2 = q
