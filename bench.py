@@ -65,6 +65,19 @@ def make_workload(name: str):
         w['storage'] = 'f32'
         w['label'] = 'rbc_tube_64^3_R30_50x642_f32'
         return w
+    if name in ('mix512', 'mix512_f32'):
+        # red cells and filaments in a channel with Morse excluded volume
+        w = I.mixed_suspension(shape=(512, 512, 512), n_cells=20000, n_filaments=4000, beads=50, seed=1709,
+                               steps=1000)
+        w['storage'] = 'f16' if name == 'mix512' else 'f32'
+        w['label'] = f'mixed_channel_512^3_20000x642_cells_4000x50_filaments_{w["storage"]}'
+        return w
+    if name == 'mix128':
+        # 128 x 64 x 64 copy of the mixed suspension at the same cell and filament densities
+        w = I.mixed_suspension(shape=(128, 64, 64), n_cells=39, n_filaments=16, beads=50, seed=1709, steps=1000)
+        w['storage'] = 'f16'
+        w['label'] = 'mixed_channel_128x64x64_39x642_cells_16x50_filaments_f16'
+        return w
     if name == 'serve':
         # the first case of the serving stream (the reference arm's sample)
         w = I.serving_stream(n_cases=1, seed=1708)[0]
@@ -276,13 +289,22 @@ def time_oracle(w, steps, warmup=0):
     return dict(mlups=N * steps / dt / 1e6, seconds=dt, setup_s=setup, steps=steps)
 
 
+def cpu_sample(name):
+    """The workload the FP64 oracle is timed on: the workload itself, or a
+    bounded copy where one oracle step would not finish in seconds (the
+    oracle's Morse term visits every pair of markers)."""
+    if name in ('mix512', 'mix512_f32'):
+        return make_workload('mix128')
+    return make_workload(name)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    w = make_workload(args.workload)
+    w = cpu_sample(args.workload)
     # each requested step is bounded: at most a couple of full oracle steps
     # are timed so that the whole run ends within a few minutes
     n = max(1, min(args.steps, args.ref_max_steps))
@@ -393,9 +415,10 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        r = time_oracle(w, 1)
+        ws_cpu = cpu_sample(args.workload)
+        r = time_oracle(ws_cpu, 1)
         cpu = dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
-                   sample=f'1 full coupled step of {w["label"]} (FP64 C oracle, single thread, setup excluded)',
+                   sample=f'1 full coupled step of {ws_cpu["label"]} (FP64 C oracle, single thread, setup excluded)',
                    seconds=r['seconds'])
 
     if rank == 0:
@@ -410,6 +433,7 @@ def run_ours(args):
             dtype='f32' if storage == 'f32' else f'f32 ({storage}-deviation storage)', data='synthetic',
             config=dict(workload=w['label'], lattice=[lat['nx'], lat['ny'], lat['nz']], fluid_cells=Nf,
                         touched_cells=n_touch, markers=M, bodies=len(w['bodies']), tau=lat['tau'],
+                        filaments=sum(1 for b in w['bodies'] if b['kind'] == 2), morse=w.get('morse'),
                         body_force=lat['body_force'][0], storage=storage, seed=w['seed'],
                         mflups_fluid=Nf * args.steps * ws / (ms_max / 1e3) / 1e6,
                         graph_path_ms_per_step=graph_ms / args.steps,
@@ -625,7 +649,8 @@ def main(argv=None):
     ap.add_argument('--warmup', type=int, default=20)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--workload', default='tube256',
-                    choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube160', 'tube64', 'shear32', 'serve'])
+                    choices=['tube256', 'tube256_f16', 'tube256_bf16', 'tube160', 'tube64', 'shear32', 'mix512',
+                             'mix512_f32', 'mix128', 'serve'])
     ap.add_argument('--serve-cases', type=int, default=64)
     ap.add_argument('--period-scale', type=float, default=0.05)
     ap.add_argument('--serve-slots', type=int, default=64)
