@@ -33,11 +33,15 @@ constexpr int COLLIDE_THREADS = 128;
 #define IBM_COLLIDE_MIN_BLOCKS 8  // resident blocks per SM the register budget is sized for
 #endif
 
+// The grid is one-dimensional (a row count above 65535 blocks does not fit
+// the y dimension): block b covers x chunk b % nxb of row block b / nxb,
+// x chunks of a row consecutive.
 template <int S, int ODD, int GEOM, bool DENSE>
 __global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
-                                                                int n_rows) {
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+                                                                int n_rows, int nxb) {
+  const int rb = blockIdx.x / nxb, xb = blockIdx.x - rb * nxb;
+  const int r = rb * blockDim.y + threadIdx.y;
+  const int x = xb * blockDim.x + threadIdx.x;
   if (r >= n_rows || x >= L.nx) return;
   collide_cell<S, ODD, GEOM, DENSE>(L, rows[r], x);
 }
@@ -182,13 +186,14 @@ template <int S, int GEOM>
 void launch_collide_g(const LatticeDev& L, const RowInfo* rows, int n_rows, bool odd, bool dense, cudaStream_t st) {
   const int tx = L.nx >= COLLIDE_THREADS ? COLLIDE_THREADS : ((L.nx + 31) / 32) * 32;
   const int ty = COLLIDE_THREADS / tx;
-  const dim3 block(tx, ty), grid((L.nx + tx - 1) / tx, (n_rows + ty - 1) / ty);
+  const int nxb = (L.nx + tx - 1) / tx;
+  const dim3 block(tx, ty), grid((unsigned)nxb * (unsigned)((n_rows + ty - 1) / ty));
   if (odd) {
-    if (dense) k_collide<S, 1, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows);
-    else k_collide<S, 1, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows);
+    if (dense) k_collide<S, 1, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    else k_collide<S, 1, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
   } else {
-    if (dense) k_collide<S, 0, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows);
-    else k_collide<S, 0, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows);
+    if (dense) k_collide<S, 0, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    else k_collide<S, 0, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
   }
 }
 template <int S>

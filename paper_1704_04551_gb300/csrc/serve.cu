@@ -148,12 +148,13 @@ __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_interpolate_b(const C
 // rows are grouped by geometry, one launch per geometry present.
 template <int ODD, int GEOM>
 __global__ void __launch_bounds__(SERVE_COLLIDE_TX * SERVE_COLLIDE_TY, 6)
-    k_collide_b(const CaseDev* cases, const Item* items, int n_items) {
-  const int item = blockIdx.y * blockDim.y + threadIdx.y;
+    k_collide_b(const CaseDev* cases, const Item* items, int n_items, int nxb) {
+  const int ib = blockIdx.x / nxb, xb = blockIdx.x - ib * nxb;  // one-dimensional grid, x chunks fastest
+  const int item = ib * blockDim.y + threadIdx.y;
   if (item >= n_items) return;
   const Item it = items[item];
   const CaseDev& C = cases[it.c];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = xb * blockDim.x + threadIdx.x;
   if (!C.active || x >= C.L.nx) return;
   const LatticeDev L = case_lattice(C);
   const RowInfo R = C.rows[it.i];
@@ -397,16 +398,17 @@ int rebuild(ibm_lbm_server_t* s) {
       const int first = s->geom_first[g], n_items = s->geom_first[g + 1] - first;
       if (n_items == 0) continue;
       const dim3 block(SERVE_COLLIDE_TX, SERVE_COLLIDE_TY);
-      const dim3 grid(s->max_xblocks, (n_items + SERVE_COLLIDE_TY - 1) / SERVE_COLLIDE_TY);
+      const int nxb = s->max_xblocks;
+      const dim3 grid((unsigned)nxb * (unsigned)((n_items + SERVE_COLLIDE_TY - 1) / SERVE_COLLIDE_TY));
       const Item* items = s->d_rows + first;
       const bool odd = step & 1;
       switch (g * 2 + (odd ? 1 : 0)) {
-        case 0: k_collide_b<0, GEOM_PERIODIC><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
-        case 1: k_collide_b<1, GEOM_PERIODIC><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
-        case 2: k_collide_b<0, GEOM_YWALLS><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
-        case 3: k_collide_b<1, GEOM_YWALLS><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
-        case 4: k_collide_b<0, GEOM_TUBE><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
-        default: k_collide_b<1, GEOM_TUBE><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items); break;
+        case 0: k_collide_b<0, GEOM_PERIODIC><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
+        case 1: k_collide_b<1, GEOM_PERIODIC><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
+        case 2: k_collide_b<0, GEOM_YWALLS><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
+        case 3: k_collide_b<1, GEOM_YWALLS><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
+        case 4: k_collide_b<0, GEOM_TUBE><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
+        default: k_collide_b<1, GEOM_TUBE><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
       }
     }
     if (s->n_groups)
