@@ -408,9 +408,11 @@ int prepare_morse(ibm_lbm_t* h) {
   P.rank = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
   P.sorted = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
   P.sorted_id = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
-  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id)
+  P.bin_owner = (int*)dalloc(h, h->morse_mem, sizeof(int) * P.n_bins);
+  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id || !P.bin_owner)
     return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
   CUDA_TRY(h, cudaMemset(P.count, 0, sizeof(int) * P.n_bins));
+  CUDA_TRY(h, cudaMemset(P.bin_owner, 0xff, sizeof(int) * P.n_bins));
   CUDA_TRY(h, cudaMemset(P.start, 0, sizeof(int) * ((size_t)P.n_bins + 1)));
   h->morse_ready = true;
   return IBM_LBM_OK;

@@ -149,6 +149,7 @@ struct MorseDev {
   int* rank;          // [M] position within the bin
   float4* sorted;     // [M] wrapped position, owner body (int bits in w), by bin
   int* sorted_id;     // [M] marker of each sorted slot
+  int* bin_owner;     // [n_bins] the one body all markers of a bin belong to, -2 if several, -1 if empty
   const int* owner;   // [M] body of a participating marker, -1 otherwise
 };
 

@@ -10,7 +10,9 @@
 // the counts, markers scattered into bin order (wrapped position and owner
 // body packed in a float4), then one thread per sorted marker gathers the
 // forces of the markers in the 27 bins around its own and adds them to its
-// marker force. Positions come from the stencil cache (floor + FP32
+// marker force. Each bin also records whether all its markers belong to one
+// body; a marker skips the bins that hold only markers of its own body (most
+// bins near a membrane), without reading them. Positions come from the stencil cache (floor + FP32
 // fraction), wrapped into the box on periodic axes, so separations are
 // exact to FP32 rounding of a coordinate below the box size.
 #include "common.cuh"
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_totals(MorseDev P, int n_
   if (threadIdx.x == 0) P.start[P.n_bins] = total;
 }
 
-// add the tile offsets; clear the counts for the next step
+// add the tile offsets; clear the counts for the next step and the bin
+// owners for this step's scatter
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(MorseDev P) {
   const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   const int off = P.block_sum[blockIdx.x];
@@ -129,16 +132,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(MorseDev P) {
     if (base + i < P.n_bins) {
       P.start[base + i] += off;
       P.count[base + i] = 0;
+      P.bin_owner[base + i] = -1;
     }
 }
 
 __global__ void k_morse_scatter(MorseDev P, MarkersDev m, Box B) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m.M || P.owner[k] < 0) return;
-  const int slot = P.start[P.bin_of[k]] + P.rank[k];
+  const int bin = P.bin_of[k], own = P.owner[k];
+  const int slot = P.start[bin] + P.rank[k];
   P.sorted[slot] = make_float4(wrapped_coord(m, B, 0, k), wrapped_coord(m, B, 1, k), wrapped_coord(m, B, 2, k),
-                               __int_as_float(P.owner[k]));
+                               __int_as_float(own));
   P.sorted_id[slot] = k;
+  // the first marker claims the bin; a marker of another body marks it mixed
+  const int prev = atomicCAS(P.bin_owner + bin, -1, own);
+  if (prev != -1 && prev != own) P.bin_owner[bin] = -2;
 }
 
 // Neighbour bins along one axis: first .. first + cnt - 1, taken modulo nb
@@ -183,6 +191,7 @@ __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, Marke
     for (int iy = 0; iy < ry.cnt; ++iy)
       for (int ix = 0; ix < rx.cnt; ++ix) {
         const int bin = range_bin(rx, ix, P.nb[0]) + P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
+        if (P.bin_owner[bin] == own) continue;  // only this body's markers
         const int j1 = P.start[bin + 1];
         for (int j = P.start[bin]; j < j1; ++j) {
           const float4 q = P.sorted[j];
