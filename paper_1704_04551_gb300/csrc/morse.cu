@@ -5,14 +5,17 @@
 // marker is F = -dU/dr d/r = 2 alpha D0 (e^2 - e) d/r, e = e^{-alpha (r - r0)},
 // d its separation from the other marker (nearest image on periodic axes).
 //
-// A cell list rebuilt every step: bins at least rc wide (at most 2^24 of
+// A cell list rebuilt every step: bins at least rc wide (at most 2^26 of
 // them), markers counted into bins with atomics, an exclusive prefix sum of
 // the counts, markers scattered into bin order (wrapped position and owner
 // body packed in a float4), then one thread per sorted marker gathers the
 // forces of the markers in the 27 bins around its own and adds them to its
 // marker force. Each bin also records whether all its markers belong to one
-// body; a marker skips the bins that hold only markers of its own body (most
-// bins near a membrane), without reading them. Positions come from the stencil cache (floor + FP32
+// body. Before the gather, the first marker of every occupied bin checks
+// once whether the bin or one of its 26 neighbours holds a marker of another
+// body; markers of bins with no such neighbour (most of them: a membrane's
+// own vertices fill the bins around it) return at once, and the others skip
+// empty bins and bins of their own body without reading them. Positions come from the stencil cache (floor + FP32
 // fraction), wrapped into the box on periodic axes, so separations are
 // exact to FP32 rounding of a coordinate below the box size.
 #include "common.cuh"
@@ -24,7 +27,7 @@ namespace {
 
 constexpr int MORSE_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_ITEMS = 4;  // per thread
+constexpr int SCAN_ITEMS = 8;  // per thread: tiles of 8192 bins, at most 8192 tiles (2^26 bins)
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 struct Box {
@@ -53,6 +56,7 @@ __global__ void k_morse_count(MorseDev P, MarkersDev m, Box B) {
   const int bin = b[0] + P.nb[0] * (b[1] + P.nb[1] * b[2]);
   P.bin_of[k] = bin;
   P.rank[k] = atomicAdd(P.count + bin, 1);
+  P.bin_owner[bin] = -1;  // claimed again by the scatter (bins left empty keep a stale owner, never read as a range)
 }
 
 // exclusive scan of SCAN_ITEMS values per thread across the block; returns
@@ -84,21 +88,39 @@ __device__ __forceinline__ int block_exclusive(int v, int& total) {
   return before + x - v;
 }
 
-// tile-local exclusive prefix into start[], tile totals into block_sum[]
+// padded shared-memory index: conflict-free for both the coalesced
+// (i = k * threads + t) and the per-thread contiguous (i = t * items + k) sweeps
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+// tile-local exclusive prefix into start[], tile totals into block_sum[];
+// the tile goes through shared memory so that global accesses coalesce
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(MorseDev P) {
-  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  __shared__ int sh[SCAN_TILE + SCAN_TILE / 32];
+  const int base = blockIdx.x * SCAN_TILE;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = k * SCAN_THREADS + threadIdx.x;
+    sh[pad(i)] = base + i < P.n_bins ? P.count[base + i] : 0;
+  }
+  __syncthreads();
   int v[SCAN_ITEMS], s = 0;
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    v[i] = base + i < P.n_bins ? P.count[base + i] : 0;
-    s += v[i];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = sh[pad(threadIdx.x * SCAN_ITEMS + k)];
+    s += v[k];
   }
   int total;
-  int run = block_exclusive(s, total);
+  int run = block_exclusive(s, total);  // synchronises
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    if (base + i < P.n_bins) P.start[base + i] = run;
-    run += v[i];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    sh[pad(threadIdx.x * SCAN_ITEMS + k)] = run;
+    run += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = k * SCAN_THREADS + threadIdx.x;
+    if (base + i < P.n_bins) P.start[base + i] = sh[pad(i)];
   }
   if (threadIdx.x == 0) P.block_sum[blockIdx.x] = total;
 }
@@ -122,18 +144,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_totals(MorseDev P, int n_
   if (threadIdx.x == 0) P.start[P.n_bins] = total;
 }
 
-// add the tile offsets; clear the counts for the next step and the bin
-// owners for this step's scatter
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(MorseDev P) {
-  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-  const int off = P.block_sum[blockIdx.x];
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i)
-    if (base + i < P.n_bins) {
-      P.start[base + i] += off;
-      P.count[base + i] = 0;
-      P.bin_owner[base + i] = -1;
-    }
+// add the tile offsets (one thread per bin)
+__global__ void k_scan_add(MorseDev P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.n_bins) P.start[i] += P.block_sum[i / SCAN_TILE];
 }
 
 __global__ void k_morse_scatter(MorseDev P, MarkersDev m, Box B) {
@@ -144,14 +158,15 @@ __global__ void k_morse_scatter(MorseDev P, MarkersDev m, Box B) {
   P.sorted[slot] = make_float4(wrapped_coord(m, B, 0, k), wrapped_coord(m, B, 1, k), wrapped_coord(m, B, 2, k),
                                __int_as_float(own));
   P.sorted_id[slot] = k;
+  P.count[bin] = 0;  // counts are not read again this step
   // the first marker claims the bin; a marker of another body marks it mixed
   const int prev = atomicCAS(P.bin_owner + bin, -1, own);
   if (prev != -1 && prev != own) P.bin_owner[bin] = -2;
 }
 
-// Neighbour bins along one axis: first .. first + cnt - 1, taken modulo nb
-// on periodic axes (-1, 0, +1, or all bins when there are fewer than
-// three), clipped to the axis otherwise.
+// Neighbour bins along one axis: first .. first + cnt - 1; on periodic axes
+// first = b - 1 (-1 at the low end) and indices wrap into [0, nb) (all bins
+// when there are fewer than three); on other axes the range is clipped.
 struct AxisRange {
   int first, cnt;
 };
@@ -162,7 +177,7 @@ __device__ __forceinline__ AxisRange axis_range(int b, int nb, bool periodic) {
       r.first = 0;
       r.cnt = nb;
     } else {
-      r.first = b - 1 + nb;  // kept non-negative for the modulo
+      r.first = b - 1;
       r.cnt = 3;
     }
   } else {
@@ -172,8 +187,36 @@ __device__ __forceinline__ AxisRange axis_range(int b, int nb, bool periodic) {
   return r;
 }
 __device__ __forceinline__ int range_bin(const AxisRange& r, int d, int nb) {
-  const int v = r.first + d;
-  return v >= nb ? v % nb : v;
+  const int v = r.first + d;  // in [-1, nb]
+  return v < 0 ? v + nb : (v >= nb ? v - nb : v);
+}
+
+// The first marker of each occupied bin decides whether the bin needs the
+// gather: it is mixed, or a neighbour bin holds markers of another body.
+__global__ void __launch_bounds__(MORSE_THREADS) k_morse_active(MorseDev P, Box B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.start[P.n_bins]) return;
+  const float4 p = P.sorted[s];
+  const int b0 = bin_coord(P, 0, p.x), b1 = bin_coord(P, 1, p.y), b2 = bin_coord(P, 2, p.z);
+  const int bin = b0 + P.nb[0] * (b1 + P.nb[1] * b2);
+  if (s != P.start[bin]) return;
+  const int own = P.bin_owner[bin];
+  bool active = own < 0;  // mixed
+  const AxisRange rx = axis_range(b0, P.nb[0], B.periodic[0] != 0);
+  const AxisRange ry = axis_range(b1, P.nb[1], B.periodic[1] != 0);
+  const AxisRange rz = axis_range(b2, P.nb[2], B.periodic[2] != 0);
+  for (int iz = 0; iz < rz.cnt && !active; ++iz)
+    for (int iy = 0; iy < ry.cnt && !active; ++iy) {
+      const int row = P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
+      for (int ix = 0; ix < rx.cnt; ++ix) {
+        const int bo = P.bin_owner[row + range_bin(rx, ix, P.nb[0])];
+        if (bo != -1 && bo != own) {
+          active = true;
+          break;
+        }
+      }
+    }
+  P.bin_active[bin] = active ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, MarkersDev m, Box B) {
@@ -181,17 +224,20 @@ __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, Marke
   if (s >= P.start[P.n_bins]) return;
   const float4 p = P.sorted[s];
   const int own = __float_as_int(p.w);
-  const float pc[3] = {p.x, p.y, p.z};
-  const AxisRange rx = axis_range(bin_coord(P, 0, pc[0]), P.nb[0], B.periodic[0] != 0);
-  const AxisRange ry = axis_range(bin_coord(P, 1, pc[1]), P.nb[1], B.periodic[1] != 0);
-  const AxisRange rz = axis_range(bin_coord(P, 2, pc[2]), P.nb[2], B.periodic[2] != 0);
+  const int b0 = bin_coord(P, 0, p.x), b1 = bin_coord(P, 1, p.y), b2 = bin_coord(P, 2, p.z);
+  if (!P.bin_active[b0 + P.nb[0] * (b1 + P.nb[1] * b2)]) return;  // no other body in reach
+  const AxisRange rx = axis_range(b0, P.nb[0], B.periodic[0] != 0);
+  const AxisRange ry = axis_range(b1, P.nb[1], B.periodic[1] != 0);
+  const AxisRange rz = axis_range(b2, P.nb[2], B.periodic[2] != 0);
   const float hx = 0.5f * B.n[0], hy = 0.5f * B.n[1], hz = 0.5f * B.n[2];
   float fx = 0.f, fy = 0.f, fz = 0.f;
   for (int iz = 0; iz < rz.cnt; ++iz)
-    for (int iy = 0; iy < ry.cnt; ++iy)
+    for (int iy = 0; iy < ry.cnt; ++iy) {
+      const int row = P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
       for (int ix = 0; ix < rx.cnt; ++ix) {
-        const int bin = range_bin(rx, ix, P.nb[0]) + P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
-        if (P.bin_owner[bin] == own) continue;  // only this body's markers
+        const int bin = row + range_bin(rx, ix, P.nb[0]);
+        const int bo = P.bin_owner[bin];
+        if (bo == own || bo == -1) continue;  // only this body's markers, or empty
         const int j1 = P.start[bin + 1];
         for (int j = P.start[bin]; j < j1; ++j) {
           const float4 q = P.sorted[j];
@@ -210,6 +256,7 @@ __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, Marke
           fz = fmaf(c, dz, fz);
         }
       }
+    }
   const int k = P.sorted_id[s];
   float4 F = m.F[k];
   F.x += fx;
@@ -235,8 +282,9 @@ void launch_morse(const MorseDev& P, const MarkersDev& m, int nx, int ny, int nz
   k_morse_count<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
   k_scan_tiles<<<tiles, SCAN_THREADS, 0, st>>>(P);
   k_scan_totals<<<1, SCAN_THREADS, 0, st>>>(P, tiles);
-  k_scan_add<<<tiles, SCAN_THREADS, 0, st>>>(P);
+  k_scan_add<<<(P.n_bins + 255) / 256, 256, 0, st>>>(P);
   k_morse_scatter<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
+  k_morse_active<<<grid, MORSE_THREADS, 0, st>>>(P, B);
   k_morse_force<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
 }
 
