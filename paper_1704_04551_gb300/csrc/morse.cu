@@ -191,6 +191,30 @@ __device__ __forceinline__ int range_bin(const AxisRange& r, int d, int nb) {
   return v < 0 ? v + nb : (v >= nb ? v - nb : v);
 }
 
+// Bins around (b0, b1, b2) whose owner is neither `own` nor empty, as a
+// 27-bit mask (bit ix + 3 iy + 9 iz); the 27 owner loads are independent.
+__device__ __forceinline__ unsigned foreign_bins(const MorseDev& P, const Box& B, int b0, int b1, int b2, int own,
+                                                 AxisRange& rx, AxisRange& ry, AxisRange& rz) {
+  rx = axis_range(b0, P.nb[0], B.periodic[0] != 0);
+  ry = axis_range(b1, P.nb[1], B.periodic[1] != 0);
+  rz = axis_range(b2, P.nb[2], B.periodic[2] != 0);
+  unsigned mask = 0u;
+#pragma unroll
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy) {
+      if (iz >= rz.cnt || iy >= ry.cnt) continue;
+      const int row = P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
+#pragma unroll
+      for (int ix = 0; ix < 3; ++ix) {
+        if (ix >= rx.cnt) continue;
+        const int bo = P.bin_owner[row + range_bin(rx, ix, P.nb[0])];
+        if (bo != own && bo != -1) mask |= 1u << (ix + 3 * iy + 9 * iz);
+      }
+    }
+  return mask;
+}
+
 // The first marker of each occupied bin decides whether the bin needs the
 // gather: it is mixed, or a neighbour bin holds markers of another body.
 __global__ void __launch_bounds__(MORSE_THREADS) k_morse_active(MorseDev P, Box B) {
@@ -201,21 +225,8 @@ __global__ void __launch_bounds__(MORSE_THREADS) k_morse_active(MorseDev P, Box 
   const int bin = b0 + P.nb[0] * (b1 + P.nb[1] * b2);
   if (s != P.start[bin]) return;
   const int own = P.bin_owner[bin];
-  bool active = own < 0;  // mixed
-  const AxisRange rx = axis_range(b0, P.nb[0], B.periodic[0] != 0);
-  const AxisRange ry = axis_range(b1, P.nb[1], B.periodic[1] != 0);
-  const AxisRange rz = axis_range(b2, P.nb[2], B.periodic[2] != 0);
-  for (int iz = 0; iz < rz.cnt && !active; ++iz)
-    for (int iy = 0; iy < ry.cnt && !active; ++iy) {
-      const int row = P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
-      for (int ix = 0; ix < rx.cnt; ++ix) {
-        const int bo = P.bin_owner[row + range_bin(rx, ix, P.nb[0])];
-        if (bo != -1 && bo != own) {
-          active = true;
-          break;
-        }
-      }
-    }
+  AxisRange rx, ry, rz;
+  const bool active = own < 0 || foreign_bins(P, B, b0, b1, b2, own, rx, ry, rz) != 0u;
   P.bin_active[bin] = active ? 1 : 0;
 }
 
@@ -226,37 +237,34 @@ __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, Marke
   const int own = __float_as_int(p.w);
   const int b0 = bin_coord(P, 0, p.x), b1 = bin_coord(P, 1, p.y), b2 = bin_coord(P, 2, p.z);
   if (!P.bin_active[b0 + P.nb[0] * (b1 + P.nb[1] * b2)]) return;  // no other body in reach
-  const AxisRange rx = axis_range(b0, P.nb[0], B.periodic[0] != 0);
-  const AxisRange ry = axis_range(b1, P.nb[1], B.periodic[1] != 0);
-  const AxisRange rz = axis_range(b2, P.nb[2], B.periodic[2] != 0);
+  AxisRange rx, ry, rz;
+  unsigned mask = foreign_bins(P, B, b0, b1, b2, own, rx, ry, rz);
   const float hx = 0.5f * B.n[0], hy = 0.5f * B.n[1], hz = 0.5f * B.n[2];
   float fx = 0.f, fy = 0.f, fz = 0.f;
-  for (int iz = 0; iz < rz.cnt; ++iz)
-    for (int iy = 0; iy < ry.cnt; ++iy) {
-      const int row = P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
-      for (int ix = 0; ix < rx.cnt; ++ix) {
-        const int bin = row + range_bin(rx, ix, P.nb[0]);
-        const int bo = P.bin_owner[bin];
-        if (bo == own || bo == -1) continue;  // only this body's markers, or empty
-        const int j1 = P.start[bin + 1];
-        for (int j = P.start[bin]; j < j1; ++j) {
-          const float4 q = P.sorted[j];
-          if (__float_as_int(q.w) == own) continue;
-          float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-          if (B.periodic[0]) dx = dx > hx ? dx - B.n[0] : (dx < -hx ? dx + B.n[0] : dx);
-          if (B.periodic[1]) dy = dy > hy ? dy - B.n[1] : (dy < -hy ? dy + B.n[1] : dy);
-          if (B.periodic[2]) dz = dz > hz ? dz - B.n[2] : (dz < -hz ? dz + B.n[2] : dz);
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          if (!(r2 < P.rc2) || r2 == 0.f) continue;
-          const float r = sqrtf(r2);
-          const float e = expf(-P.alpha * (r - P.r0));
-          const float c = 2.0f * P.alpha * P.D0 * (e * e - e) / r;
-          fx = fmaf(c, dx, fx);
-          fy = fmaf(c, dy, fy);
-          fz = fmaf(c, dz, fz);
-        }
-      }
+  while (mask) {
+    const int t = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    const int ix = t % 3, iy = (t / 3) % 3, iz = t / 9;
+    const int bin = range_bin(rx, ix, P.nb[0]) +
+                    P.nb[0] * (range_bin(ry, iy, P.nb[1]) + P.nb[1] * range_bin(rz, iz, P.nb[2]));
+    const int j1 = P.start[bin + 1];
+    for (int j = P.start[bin]; j < j1; ++j) {
+      const float4 q = P.sorted[j];
+      if (__float_as_int(q.w) == own) continue;
+      float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+      if (B.periodic[0]) dx = dx > hx ? dx - B.n[0] : (dx < -hx ? dx + B.n[0] : dx);
+      if (B.periodic[1]) dy = dy > hy ? dy - B.n[1] : (dy < -hy ? dy + B.n[1] : dy);
+      if (B.periodic[2]) dz = dz > hz ? dz - B.n[2] : (dz < -hz ? dz + B.n[2] : dz);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 < P.rc2) || r2 == 0.f) continue;
+      const float r = sqrtf(r2);
+      const float e = expf(-P.alpha * (r - P.r0));
+      const float c = 2.0f * P.alpha * P.D0 * (e * e - e) / r;
+      fx = fmaf(c, dx, fx);
+      fy = fmaf(c, dy, fy);
+      fz = fmaf(c, dz, fz);
     }
+  }
   const int k = P.sorted_id[s];
   float4 F = m.F[k];
   F.x += fx;
