@@ -409,9 +409,7 @@ int prepare_morse(ibm_lbm_t* h) {
   P.sorted = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
   P.sorted_id = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
   P.bin_owner = (int*)dalloc(h, h->morse_mem, sizeof(int) * P.n_bins);
-  P.bin_active = (unsigned char*)dalloc(h, h->morse_mem, (size_t)P.n_bins);
-  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id || !P.bin_owner ||
-      !P.bin_active)
+  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id || !P.bin_owner)
     return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
   CUDA_TRY(h, cudaMemset(P.count, 0, sizeof(int) * P.n_bins));
   CUDA_TRY(h, cudaMemset(P.bin_owner, 0xff, sizeof(int) * P.n_bins));

@@ -150,7 +150,6 @@ struct MorseDev {
   float4* sorted;     // [M] wrapped position, owner body (int bits in w), by bin
   int* sorted_id;     // [M] marker of each sorted slot
   int* bin_owner;     // [n_bins] the one body all markers of a bin belong to, -2 if several, -1 if empty
-  unsigned char* bin_active;  // [n_bins] occupied bin with a marker of another body in reach (this step)
   const int* owner;   // [M] body of a participating marker, -1 otherwise
 };
 

@@ -11,11 +11,9 @@
 // body packed in a float4), then one thread per sorted marker gathers the
 // forces of the markers in the 27 bins around its own and adds them to its
 // marker force. Each bin also records whether all its markers belong to one
-// body. Before the gather, the first marker of every occupied bin checks
-// once whether the bin or one of its 26 neighbours holds a marker of another
-// body; markers of bins with no such neighbour (most of them: a membrane's
-// own vertices fill the bins around it) return at once, and the others skip
-// empty bins and bins of their own body without reading them. Positions come from the stencil cache (floor + FP32
+// body: a marker first loads the owners of its 27 neighbour bins (independent
+// loads, kept as a bit mask) and then reads only the bins that hold markers
+// of another body (a membrane's own vertices fill most bins around it). Positions come from the stencil cache (floor + FP32
 // fraction), wrapped into the box on periodic axes, so separations are
 // exact to FP32 rounding of a coordinate below the box size.
 #include "common.cuh"
@@ -215,28 +213,12 @@ __device__ __forceinline__ unsigned foreign_bins(const MorseDev& P, const Box& B
   return mask;
 }
 
-// The first marker of each occupied bin decides whether the bin needs the
-// gather: it is mixed, or a neighbour bin holds markers of another body.
-__global__ void __launch_bounds__(MORSE_THREADS) k_morse_active(MorseDev P, Box B) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= P.start[P.n_bins]) return;
-  const float4 p = P.sorted[s];
-  const int b0 = bin_coord(P, 0, p.x), b1 = bin_coord(P, 1, p.y), b2 = bin_coord(P, 2, p.z);
-  const int bin = b0 + P.nb[0] * (b1 + P.nb[1] * b2);
-  if (s != P.start[bin]) return;
-  const int own = P.bin_owner[bin];
-  AxisRange rx, ry, rz;
-  const bool active = own < 0 || foreign_bins(P, B, b0, b1, b2, own, rx, ry, rz) != 0u;
-  P.bin_active[bin] = active ? 1 : 0;
-}
-
 __global__ void __launch_bounds__(MORSE_THREADS) k_morse_force(MorseDev P, MarkersDev m, Box B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.start[P.n_bins]) return;
   const float4 p = P.sorted[s];
   const int own = __float_as_int(p.w);
   const int b0 = bin_coord(P, 0, p.x), b1 = bin_coord(P, 1, p.y), b2 = bin_coord(P, 2, p.z);
-  if (!P.bin_active[b0 + P.nb[0] * (b1 + P.nb[1] * b2)]) return;  // no other body in reach
   AxisRange rx, ry, rz;
   unsigned mask = foreign_bins(P, B, b0, b1, b2, own, rx, ry, rz);
   const float hx = 0.5f * B.n[0], hy = 0.5f * B.n[1], hz = 0.5f * B.n[2];
@@ -292,7 +274,6 @@ void launch_morse(const MorseDev& P, const MarkersDev& m, int nx, int ny, int nz
   k_scan_totals<<<1, SCAN_THREADS, 0, st>>>(P, tiles);
   k_scan_add<<<(P.n_bins + 255) / 256, 256, 0, st>>>(P);
   k_morse_scatter<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
-  k_morse_active<<<grid, MORSE_THREADS, 0, st>>>(P, B);
   k_morse_force<<<grid, MORSE_THREADS, 0, st>>>(P, m, B);
 }
 
