@@ -319,6 +319,11 @@ void ora_stage_spread(ora_t* o) {
 
 void ora_stage_interpolate(ora_t* o) {
   int64_t N = o->N, M = o->M;
+  /* markers of direct-forcing rigid bodies follow the body, not the fluid */
+  char* fixed = (char*)calloc(M ? M : 1, 1);
+  for (int b = 0; b < o->nb; ++b)
+    if (o->bodies[b].kind == 3)
+      for (int64_t k = o->bodies[b].first; k < o->bodies[b].first + o->bodies[b].count; ++k) fixed[k] = 1;
   for (int64_t k = 0; k < M; ++k) {
     double X[3] = {o->X[k], o->X[M + k], o->X[2 * M + k]};
     int base[3];
@@ -335,9 +340,10 @@ void ora_stage_interpolate(ora_t* o) {
         }
     for (int a = 0; a < 3; ++a) {
       o->U[a * M + k] = U[a];
-      o->X[a * M + k] = X[a] + U[a];
+      if (!fixed[k]) o->X[a * M + k] = X[a] + U[a];
     }
   }
+  free(fixed);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -553,7 +559,7 @@ int ora_set_bodies(ora_t* o, int32_t nb, const ora_body* bodies, int64_t M, cons
     if (B->first < 0 || B->count < 0 || B->first + B->count > M) return -1;
     if (B->kind == 0 && B->count != o->nv) return -2;
     if (B->kind == 2 && (B->count < 2 || !(B->l0 > 0.0))) return -3;
-    if (B->kind == 1) {
+    if (B->kind == 1 || B->kind == 3) {
       double R[3][3];
       quat_matrix(B->quat, R);
       for (int64_t k = B->first; k < B->first + B->count; ++k) {
@@ -578,27 +584,9 @@ void ora_set_marker_forces(ora_t* o, const double* F) {
 
 void ora_get_body(const ora_t* o, int32_t b, ora_body* out) { *out = o->bodies[b]; }
 
-/* Rigid body: tether each marker to its body-fixed reference point (penalty
- * reading of the rigid FSI coupling, Sec. 2.3); the reaction gives the
- * body's force and torque, then one explicit Newton-Euler step. */
-static void rigid_forces(ora_t* o, ora_body* B) {
-  int64_t M = o->M;
-  double R[3][3];
-  quat_matrix(B->quat, R);
-  double FB[3] = {0, 0, 0}, TB[3] = {0, 0, 0};
-  for (int64_t k = B->first; k < B->first + B->count; ++k) {
-    double r[3] = {o->ref[k], o->ref[M + k], o->ref[2 * M + k]};
-    double rw[3], d[3], f[3], t[3];
-    for (int a = 0; a < 3; ++a) rw[a] = R[a][0] * r[0] + R[a][1] * r[1] + R[a][2] * r[2];
-    for (int a = 0; a < 3; ++a) {
-      d[a] = o->X[a * M + k] - (B->center[a] + rw[a]);
-      o->F[a * M + k] = -B->kappa * d[a];
-      f[a] = B->kappa * d[a];
-      FB[a] += f[a];
-    }
-    cross3(rw, f, t);
-    for (int a = 0; a < 3; ++a) TB[a] += t[a];
-  }
+/* One explicit Newton-Euler step of a rigid body from its total force FB and
+ * torque TB (world frame, about the centre); R the rotation before the step. */
+static void rigid_update(ora_body* B, double R[3][3], const double FB[3], const double TB[3]) {
   for (int a = 0; a < 3; ++a) {
     B->vel[a] += FB[a] / B->mass;
     B->center[a] += B->vel[a];
@@ -621,6 +609,66 @@ static void rigid_forces(ora_t* o, ora_body* B) {
   for (int a = 0; a < 4; ++a) { B->quat[a] += dq[a]; n += B->quat[a] * B->quat[a]; }
   n = sqrt(n);
   for (int a = 0; a < 4; ++a) B->quat[a] /= n;
+}
+
+/* Rigid body: tether each marker to its body-fixed reference point (penalty
+ * reading of the rigid FSI coupling, Sec. 2.3); the reaction gives the
+ * body's force and torque, then one explicit Newton-Euler step. */
+static void rigid_forces(ora_t* o, ora_body* B) {
+  int64_t M = o->M;
+  double R[3][3];
+  quat_matrix(B->quat, R);
+  double FB[3] = {0, 0, 0}, TB[3] = {0, 0, 0};
+  for (int64_t k = B->first; k < B->first + B->count; ++k) {
+    double r[3] = {o->ref[k], o->ref[M + k], o->ref[2 * M + k]};
+    double rw[3], d[3], f[3], t[3];
+    for (int a = 0; a < 3; ++a) rw[a] = R[a][0] * r[0] + R[a][1] * r[1] + R[a][2] * r[2];
+    for (int a = 0; a < 3; ++a) {
+      d[a] = o->X[a * M + k] - (B->center[a] + rw[a]);
+      o->F[a * M + k] = -B->kappa * d[a];
+      f[a] = B->kappa * d[a];
+      FB[a] += f[a];
+    }
+    cross3(rw, f, t);
+    for (int a = 0; a < 3; ++a) TB[a] += t[a];
+  }
+  rigid_update(B, R, FB, TB);
+}
+
+/* Rigid body with the paper's direct FSI forcing (Eq. FSIRigid): the force
+ * density on the solid at a marker is rho_f (u(X) - U(X)) / dt, u the fluid
+ * velocity interpolated at the marker (Eq. ibmVelocityInterpret, the last
+ * interpolation), U = V + omega x (X - C) the body's velocity there; as a
+ * nodal force it is weighted by the volume the marker stands for, kappa
+ * (rho_f = 1, dt = 1). The fluid receives the opposite force; the sum gives
+ * the body's force and torque, one explicit Newton-Euler step, and the
+ * markers are moved rigidly to the new pose. */
+static void rigid_direct_forces(ora_t* o, ora_body* B) {
+  int64_t M = o->M;
+  double R[3][3];
+  quat_matrix(B->quat, R);
+  double FB[3] = {0, 0, 0}, TB[3] = {0, 0, 0};
+  for (int64_t k = B->first; k < B->first + B->count; ++k) {
+    double r[3] = {o->ref[k], o->ref[M + k], o->ref[2 * M + k]};
+    double rw[3], us[3], f[3], t[3];
+    for (int a = 0; a < 3; ++a) rw[a] = R[a][0] * r[0] + R[a][1] * r[1] + R[a][2] * r[2];
+    cross3(B->omega, rw, us);
+    for (int a = 0; a < 3; ++a) {
+      us[a] += B->vel[a];
+      f[a] = B->kappa * (o->U[a * M + k] - us[a]);
+      o->F[a * M + k] = -f[a];
+      FB[a] += f[a];
+    }
+    cross3(rw, f, t);
+    for (int a = 0; a < 3; ++a) TB[a] += t[a];
+  }
+  rigid_update(B, R, FB, TB);
+  quat_matrix(B->quat, R);
+  for (int64_t k = B->first; k < B->first + B->count; ++k) {
+    double r[3] = {o->ref[k], o->ref[M + k], o->ref[2 * M + k]};
+    for (int a = 0; a < 3; ++a)
+      o->X[a * M + k] = B->center[a] + R[a][0] * r[0] + R[a][1] * r[1] + R[a][2] * r[2];
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -785,6 +833,8 @@ void ora_stage_forces(ora_t* o) {
     ora_body* B = &o->bodies[b];
     if (B->kind == 1) {
       rigid_forces(o, B);
+    } else if (B->kind == 3) {
+      rigid_direct_forces(o, B);
     } else if (B->kind == 0) {
       int64_t nv = o->nv;
       double* Xb = (double*)malloc(sizeof(double) * 3 * nv);

@@ -37,7 +37,8 @@ typedef struct {
 typedef struct {
   int32_t kind;         /* 0 membrane (Eq. membrane-potential), 1 rigid (penalty tether),
                            2 filament (bead chain: Eq. inPlanePotential bonds, Eq.
-                           bendingEnergyWorm angles) */
+                           bendingEnergyWorm angles), 3 rigid with the direct FSI
+                           forcing of Eq. FSIRigid (kappa = volume per marker) */
   int32_t pad;
   int64_t first, count; /* marker range */
   double kBT_p, k_b, k_l, k_g, k_v;   /* membrane moduli, lattice units */
