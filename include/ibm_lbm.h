@@ -61,7 +61,7 @@ typedef enum {
 
 enum { IBM_LBM_STORE_F32 = 0, IBM_LBM_STORE_F16_DEV = 1, IBM_LBM_STORE_BF16_DEV = 2 };
 enum { IBM_LBM_GEOM_PERIODIC = 0, IBM_LBM_GEOM_YWALLS = 1, IBM_LBM_GEOM_TUBE = 2 };
-enum { IBM_LBM_BODY_MEMBRANE = 0, IBM_LBM_BODY_RIGID = 1, IBM_LBM_BODY_FILAMENT = 2 };
+enum { IBM_LBM_BODY_MEMBRANE = 0, IBM_LBM_BODY_RIGID = 1, IBM_LBM_BODY_FILAMENT = 2, IBM_LBM_BODY_RIGID_DIRECT = 3 };
 enum { IBM_LBM_STAGE_FORCES = 0, IBM_LBM_STAGE_SPREAD = 1, IBM_LBM_STAGE_COLLIDE = 2,
        IBM_LBM_STAGE_INTERP = 3 };
 
@@ -97,7 +97,14 @@ typedef struct {
  * bodies tether each marker to a body-fixed point (penalty reading of the
  * rigid coupling of Sec. 2.3, Eq. FSIRigid): force on the fluid
  * F_k = -kappa (X_k - X_k^ref), reaction on the body, explicit Newton-Euler
- * update of the pose. Filaments (polymer particles of Sec. 2.2) are bead
+ * update of the pose. Direct-forcing rigid bodies use the paper's own FSI
+ * force (Eq. FSIRigid): the force density on the solid at a marker is
+ * rho_f (u(X) - U(X))/dt, u the fluid velocity interpolated there at the
+ * last interpolation, U = V + omega x (X - C) the body's velocity; each
+ * marker stands for a volume kappa (rho_f = dt = 1, so the nodal force on
+ * the solid is kappa (u - U)), the fluid receives the opposite force, and
+ * after the Newton-Euler update the markers are moved rigidly to the new
+ * pose (they are not advected by the fluid). Filaments (polymer particles of Sec. 2.2) are bead
  * chains in marker order (count >= 2): each bond has the stretching energy
  * of Eq. inPlanePotential with l_m = 2 l0 and k_p = 1.25 (kBT/p) l0^2 (no
  * force at the rest length), each interior bead the bending energy
@@ -111,7 +118,7 @@ typedef struct {
                                         area, volume moduli (Eqs. inPlanePotential,
                                         bendingEnergy, areaEnergy, volumeEnergy);
                                         filament: kBT/p and k_b */
-  double kappa;                 /* rigid: tether stiffness */
+  double kappa;                 /* rigid: tether stiffness; rigid direct: volume per marker */
   double mass, inertia[3];      /* rigid: mass and principal moments (body frame) */
   double center[3], quat[4];    /* rigid: centre, unit quaternion (w,x,y,z) body->world */
   double vel[3], omega[3];      /* rigid: velocity, angular velocity (world frame) */

@@ -629,7 +629,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
       if (!mesh) return fail(h, IBM_LBM_E_ARG, "set_markers: membrane body without a mesh");
       if (B.count != mesh->n_vertices)
         return fail(h, IBM_LBM_E_ARG, "set_markers: membrane marker count != mesh vertex count");
-    } else if (B.kind == IBM_LBM_BODY_RIGID) {
+    } else if (B.kind == IBM_LBM_BODY_RIGID || B.kind == IBM_LBM_BODY_RIGID_DIRECT) {
       any_rigid = true;
       if (!(B.mass > 0) || !(B.inertia[0] > 0) || !(B.inertia[1] > 0) || !(B.inertia[2] > 0) || !(B.kappa >= 0))
         return fail(h, IBM_LBM_E_ARG, "set_markers: rigid body needs mass, inertia > 0 and kappa >= 0");
@@ -671,7 +671,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     std::vector<double> ref(3 * (size_t)M, 0.0);
     for (int b = 0; b < n_bodies; ++b) {
       const ibm_lbm_body& B = bodies[b];
-      if (B.kind != IBM_LBM_BODY_RIGID) continue;
+      if (B.kind != IBM_LBM_BODY_RIGID && B.kind != IBM_LBM_BODY_RIGID_DIRECT) continue;
       double R[3][3];
       quat_matrix(B.quat, R);
       for (int64_t k = B.first; k < B.first + B.count; ++k) {
@@ -707,8 +707,9 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     std::vector<int> own((size_t)std::max(M, 1), -1);
     for (int b = 0; b < n_bodies; ++b) {
       const int kind = bodies[b].kind;
-      (kind == IBM_LBM_BODY_MEMBRANE ? mem : kind == IBM_LBM_BODY_RIGID ? rig : fil).push_back(b);
-      if (kind != IBM_LBM_BODY_RIGID)
+      const bool rigid = kind == IBM_LBM_BODY_RIGID || kind == IBM_LBM_BODY_RIGID_DIRECT;
+      (kind == IBM_LBM_BODY_MEMBRANE ? mem : rigid ? rig : fil).push_back(b);
+      if (!rigid)
         for (int64_t k = bodies[b].first; k < bodies[b].first + bodies[b].count; ++k) own[k] = b;
     }
     h->n_membranes = (int)mem.size();
@@ -774,17 +775,21 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   // transfer groups: bodies in chunks of BODY_GROUP, tracer runs in chunks of TRACER_GROUP
   {
     std::vector<MarkerGroup> groups;
-    std::vector<std::pair<int64_t, int64_t>> cuts = ranges;  // sorted body ranges
+    std::vector<std::pair<int64_t, int>> cuts;  // (first marker, body) in marker order
+    for (int b = 0; b < n_bodies; ++b) cuts.push_back({bodies[b].first, b});
+    std::sort(cuts.begin(), cuts.end());
     int64_t pos = 0;
-    auto add_run = [&](int64_t a, int64_t b, int step) {
-      for (int64_t s0 = a; s0 < b; s0 += step) groups.push_back({(int)s0, (int)std::min<int64_t>(step, b - s0)});
+    auto add_run = [&](int64_t a, int64_t b, int step, int flags) {
+      for (int64_t s0 = a; s0 < b; s0 += step)
+        groups.push_back({(int)s0, (int)std::min<int64_t>(step, b - s0), flags});
     };
-    for (auto& r : cuts) {
-      add_run(pos, r.first, TRACER_GROUP);
-      add_run(r.first, r.second, BODY_GROUP);
-      pos = r.second;
+    for (auto& c : cuts) {
+      const ibm_lbm_body& B = bodies[c.second];
+      add_run(pos, B.first, TRACER_GROUP, 0);
+      add_run(B.first, B.first + B.count, BODY_GROUP, B.kind == IBM_LBM_BODY_RIGID_DIRECT ? GROUP_FIXED : 0);
+      pos = B.first + B.count;
     }
-    add_run(pos, n_markers, TRACER_GROUP);
+    add_run(pos, n_markers, TRACER_GROUP, 0);
     h->n_groups = (int)groups.size();
     if ((rc = upload<MarkerGroup>(h, h->marker_mem, &h->groups, groups.data(), groups.size()))) return rc;
     h->boxes = (int4*)dalloc(h, h->marker_mem, sizeof(int4) * 2 * std::max<size_t>(1, groups.size()));

@@ -81,7 +81,9 @@ struct RowInfo {
 // kernels (a body, or part of one, or a run of passive tracers).
 struct MarkerGroup {
   int first, count;
+  int flags;  // GROUP_FIXED: positions set by a rigid body, not advected
 };
+constexpr int GROUP_FIXED = 1;
 
 // Solid test of a node with wrapped x and (for walls/tube) raw y, z.
 __device__ __forceinline__ bool solid_yz(const LatticeDev& L, int y, int z) {
@@ -183,5 +185,12 @@ struct MarkersDev {
   int* cell;          // [3][M]
   float* frac;        // [3][M]
 };
+
+// Stencil cache of one marker coordinate: floor and fractional part.
+__device__ __forceinline__ void cache_coord(const MarkersDev& m, size_t off, double X) {
+  const double f = floor(X);
+  m.cell[off] = (int)f;
+  m.frac[off] = (float)(X - f);
+}
 
 }  // namespace ibm

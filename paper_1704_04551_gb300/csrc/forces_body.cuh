@@ -330,6 +330,8 @@ __device__ __forceinline__ void filament_block(const MarkersDev& m, const BodyDe
   }
 }
 
+__device__ __forceinline__ void rigid_update(BodyDev* B, const double R[3][3], const double* sh);
+
 // Tether forces and Newton-Euler update of one rigid body by the whole
 // thread block. sh: [6 * 32] doubles.
 __device__ __forceinline__ void rigid_block(const MarkersDev& m, BodyDev* B, double* sh) {
@@ -343,15 +345,28 @@ __device__ __forceinline__ void rigid_block(const MarkersDev& m, BodyDev* B, dou
   }
   const double C0 = B->center[0], C1 = B->center[1], C2 = B->center[2];
   const double kappa = B->kappa;
+  const bool direct = B->kind == 3;
+  const double V0 = B->vel[0], V1 = B->vel[1], V2 = B->vel[2];
+  const double O0 = B->omega[0], O1 = B->omega[1], O2 = B->omega[2];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int k = B->first + threadIdx.x; k < B->first + B->count; k += blockDim.x) {
     const double r0 = m.ref[k], r1 = m.ref[M + k], r2 = m.ref[2 * M + k];
     const double w0 = R[0][0] * r0 + R[0][1] * r1 + R[0][2] * r2;
     const double w1 = R[1][0] * r0 + R[1][1] * r1 + R[1][2] * r2;
     const double w2 = R[2][0] * r0 + R[2][1] * r1 + R[2][2] * r2;
-    const double d0 = m.X[k] - (C0 + w0), d1 = m.X[M + k] - (C1 + w1), d2 = m.X[2 * M + k] - (C2 + w2);
-    m.F[k] = make_float4((float)(-kappa * d0), (float)(-kappa * d1), (float)(-kappa * d2), 0.f);
-    const double f0 = kappa * d0, f1 = kappa * d1, f2 = kappa * d2;
+    double f0, f1, f2;  // force on the solid
+    if (direct) {
+      // Eq. FSIRigid: kappa (u(X) - (V + omega x r)), u the last interpolated velocity
+      const float4 u = m.U[k];
+      f0 = kappa * ((double)u.x - (V0 + O1 * w2 - O2 * w1));
+      f1 = kappa * ((double)u.y - (V1 + O2 * w0 - O0 * w2));
+      f2 = kappa * ((double)u.z - (V2 + O0 * w1 - O1 * w0));
+    } else {
+      f0 = kappa * (m.X[k] - (C0 + w0));
+      f1 = kappa * (m.X[M + k] - (C1 + w1));
+      f2 = kappa * (m.X[2 * M + k] - (C2 + w2));
+    }
+    m.F[k] = make_float4((float)(-f0), (float)(-f1), (float)(-f2), 0.f);
     acc[0] += f0; acc[1] += f1; acc[2] += f2;
     acc[3] += w1 * f2 - w2 * f1;
     acc[4] += w2 * f0 - w0 * f2;
@@ -366,7 +381,39 @@ __device__ __forceinline__ void rigid_block(const MarkersDev& m, BodyDev* B, dou
   if (lane == 0)
     for (int k = 0; k < 6; ++k) sh[k * 32 + warp] = acc[k];
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x == 0) {
+    rigid_update(B, R, sh);
+    if (direct)  // hand the new pose to the block through shared memory
+      for (int a = 0; a < 4; ++a) sh[a] = B->quat[a];
+    if (direct)
+      for (int a = 0; a < 3; ++a) sh[4 + a] = B->center[a];
+  }
+  if (!direct) return;
+  __syncthreads();
+  // direct forcing: the markers follow the body to its new pose
+  double Q[3][3];
+  {
+    const double w = sh[0], x = sh[1], y = sh[2], z = sh[3];
+    Q[0][0] = 1 - 2 * (y * y + z * z); Q[0][1] = 2 * (x * y - w * z);     Q[0][2] = 2 * (x * z + w * y);
+    Q[1][0] = 2 * (x * y + w * z);     Q[1][1] = 1 - 2 * (x * x + z * z); Q[1][2] = 2 * (y * z - w * x);
+    Q[2][0] = 2 * (x * z - w * y);     Q[2][1] = 2 * (y * z + w * x);     Q[2][2] = 1 - 2 * (x * x + y * y);
+  }
+  const double Cn[3] = {sh[4], sh[5], sh[6]};
+  for (int k = B->first + threadIdx.x; k < B->first + B->count; k += blockDim.x) {
+    const double r0 = m.ref[k], r1 = m.ref[M + k], r2 = m.ref[2 * M + k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double X = Cn[a] + Q[a][0] * r0 + Q[a][1] * r1 + Q[a][2] * r2;
+      m.X[a * M + k] = X;
+      cache_coord(m, a * M + k, X);
+    }
+  }
+}
+
+// One explicit Newton-Euler step of a rigid body from the per-warp partial
+// sums of its force and torque in sh (thread 0 of the block).
+__device__ __forceinline__ void rigid_update(BodyDev* B, const double R[3][3], const double* sh) {
+  double acc[6];
   for (int k = 0; k < 6; ++k) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[k * 32 + w];

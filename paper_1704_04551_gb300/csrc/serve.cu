@@ -344,7 +344,8 @@ int rebuild(ibm_lbm_server_t* s) {
     if (h->m.M > 0)
       for (int g = 0; g < h->n_groups; ++g) groups.push_back({i, g});
     for (int b = 0; b < h->n_bodies; ++b) {
-      if (h->h_bodies[b].kind == IBM_LBM_BODY_RIGID) rigid.push_back({i, b});
+      const int kind = h->h_bodies[b].kind;
+      if (kind == IBM_LBM_BODY_RIGID || kind == IBM_LBM_BODY_RIGID_DIRECT) rigid.push_back({i, b});
       else membranes.push_back({i, b});
     }
     if (h->n_membranes > 0)
@@ -532,8 +533,8 @@ int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t*
   if (in->n_bodies) c->bodies.assign(in->bodies, in->bodies + in->n_bodies);
   bool rigid = false;
   for (auto& b : c->bodies) {
-    rigid |= b.kind == IBM_LBM_BODY_RIGID;
-    if (b.kind != IBM_LBM_BODY_RIGID && b.kind != IBM_LBM_BODY_MEMBRANE)
+    rigid |= b.kind == IBM_LBM_BODY_RIGID || b.kind == IBM_LBM_BODY_RIGID_DIRECT;
+    if (b.kind == IBM_LBM_BODY_FILAMENT)
       return sfail(s, IBM_LBM_E_ARG, "submit: served cases hold membranes, rigid bodies and tracers");
   }
   if (in->mesh) {

@@ -223,12 +223,6 @@ __device__ inline void group_box(const MarkersDev& m, const MarkerGroup& G, int4
 // FP32 rate).
 __device__ __forceinline__ int to_fixed(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
 
-// Stencil cache of one coordinate: floor and fractional part.
-__device__ __forceinline__ void cache_coord(const MarkersDev& m, size_t off, double X) {
-  const double f = floor(X);
-  m.cell[off] = (int)f;
-  m.frac[off] = (float)(X - f);
-}
 
 // Lane mapping of a row-by-row sweep over a box whose rows hold dx cells:
 // rows shorter than a warp are packed rpw to a warp (lane -> sub-row sub,
@@ -432,7 +426,7 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     }
     if (!active) continue;
     if (a == 0) m.U[k] = make_float4(ux, uy, uz, 0.f);
-    if (a < 3) {
+    if (a < 3 && !(G.flags & GROUP_FIXED)) {
       // advection of one coordinate per lane (FP64), then its stencil cache
       const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
       const size_t off = (size_t)a * M + k;

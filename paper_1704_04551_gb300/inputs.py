@@ -25,6 +25,7 @@ import numpy as np
 BODY_MEMBRANE = 0
 BODY_RIGID = 1
 BODY_FILAMENT = 2
+BODY_RIGID_DIRECT = 3
 
 # Geometry codes.
 GEOM_PERIODIC = 0
@@ -199,9 +200,11 @@ def filament(first, n_beads, start, direction, l0=1.0, kBT_p=0.0, k_b=0.0):
     return X, _body(BODY_FILAMENT, first, n_beads, kBT_p=kBT_p, k_b=k_b, l0=l0)
 
 
-def rigid_ellipsoid(center, axes, quat, first, freq=9, kappa=0.02):
+def rigid_ellipsoid(center, axes, quat, first, freq=9, kappa=0.02, direct=False):
     """Markers on a rigid ellipsoid surface and its body record (neutrally
-    buoyant, unit fluid density)."""
+    buoyant, unit fluid density). direct=True selects the direct FSI forcing
+    (Eq. FSIRigid) with each marker standing for an equal share of the
+    surface times one lattice spacing (kappa is then ignored)."""
     S, _ = geodesic_sphere(freq)
     a, b, c = axes
     local = S * np.array([a, b, c])
@@ -209,13 +212,15 @@ def rigid_ellipsoid(center, axes, quat, first, freq=9, kappa=0.02):
     X = (local @ R.T + np.asarray(center)).T.copy()
     mass = 4.0 / 3.0 * math.pi * a * b * c
     inertia = [mass * (b * b + c * c) / 5, mass * (a * a + c * c) / 5, mass * (a * a + b * b) / 5]
-    body = _body(BODY_RIGID, first, X.shape[1], kappa=kappa, mass=mass, inertia=inertia,
-                 center=list(map(float, center)), quat=list(map(float, quat)))
+    if direct:
+        kappa = ellipsoid_area(a, b, c) / X.shape[1]
+    body = _body(BODY_RIGID_DIRECT if direct else BODY_RIGID, first, X.shape[1], kappa=kappa, mass=mass,
+                 inertia=inertia, center=list(map(float, center)), quat=list(map(float, quat)))
     return X, body
 
 
 def shear_ellipsoid(n=32, ny=None, nz=None, tau=0.8, wall_speed=0.02, axes=(6.0, 3.0, 3.0),
-                    seed=1705, kappa=0.02, freq=9, steps=500, quat=None, couette_init=False):
+                    seed=1705, kappa=0.02, freq=9, steps=500, quat=None, couette_init=False, direct=False):
     """Rigid prolate ellipsoid centred in a Couette cell: periodic x and z,
     y-walls moving at -/+ wall_speed. With couette_init the fluid starts
     from the linear wall-driven profile u_x = U (2 (y + 1/2)/H - 1) instead
@@ -225,7 +230,7 @@ def shear_ellipsoid(n=32, ny=None, nz=None, tau=0.8, wall_speed=0.02, axes=(6.0,
     rng = np.random.default_rng(seed)
     q = random_quaternion(rng) if quat is None else np.asarray(quat, dtype=np.float64)
     center = np.array([(n - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
-    X, body = rigid_ellipsoid(center, axes, q, 0, freq=freq, kappa=kappa)
+    X, body = rigid_ellipsoid(center, axes, q, 0, freq=freq, kappa=kappa, direct=direct)
     lattice = dict(nx=n, ny=ny, nz=nz, tau=tau, geometry=GEOM_YWALLS,
                    wall_u=[-wall_speed, wall_speed], tube_radius=0.0, body_force=[0.0, 0.0, 0.0])
     w = dict(name=f'shear_ellipsoid_{n}x{ny}x{nz}', lattice=lattice, mesh=None,

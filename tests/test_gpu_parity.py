@@ -246,3 +246,40 @@ def test_errors_are_reported(cuda_lib):
         sim.step(-1)
     sim.set_markers(None, [], np.zeros((3, 0)))
     sim.step(0)
+
+
+def test_rigid_direct_forcing_stage_and_coupled(cuda_lib):
+    """The paper's direct FSI forcing (Eq. FSIRigid) for a rigid ellipsoid:
+    one interpolation + forces stage in a random flow (marker forces, the
+    rigidly moved markers, the new pose), then 300 coupled steps in a
+    Couette cell, against the oracle."""
+    from paper_1704_04551_gb300.binding import Simulation
+    w = I.shear_ellipsoid(n=24, axes=(5.0, 2.5, 2.5), seed=33, direct=True)
+    sim = Simulation.from_workload(w)
+    ora = O.Oracle.from_workload(w)
+    rng = np.random.default_rng(4)
+    u = 0.01 * (2 * rng.random((3, sim.N)) - 1)
+    sim.set_lattice(None, u)
+    ora.set_equilibrium(None, u)
+    sim.stage(cuda_lib.STAGE_INTERP)
+    ora.stage_interpolate()
+    sim.stage(cuda_lib.STAGE_FORCES)
+    ora.stage_forces()
+    Xg, _, Fg = sim.markers()
+    Xo, _, Fo = ora.markers()
+    assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+    assert np.abs(Xg - Xo).max() < 1e-9
+    bg, bo = sim.bodies()[0], ora.body(0)
+    for k in ('center', 'quat', 'vel', 'omega'):
+        assert np.allclose(bg[k], bo[k], rtol=1e-5, atol=1e-10), k
+    w = I.shear_ellipsoid(n=32, steps=300, direct=True, couette_init=True)
+    sim, ora = _run_pair(w, 300)
+    _, ug = sim.fields()
+    _, uo = ora.fields()
+    assert rel_l2(ug, uo) < 1e-5
+    Xg, _, _ = sim.markers()
+    Xo, _, _ = ora.markers()
+    assert np.abs(Xg - Xo).max() < 1e-5
+    bg, bo = sim.bodies()[0], ora.body(0)
+    assert np.allclose(bg['omega'], bo['omega'], rtol=1e-3, atol=1e-9)
+    assert np.allclose(bg['quat'], bo['quat'], atol=1e-6)
