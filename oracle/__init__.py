@@ -73,6 +73,7 @@ def lib():
                      'ora_stage_interpolate'):
             getattr(L, name).argtypes = [P]
         L.ora_step.argtypes = [P, C.c_int64]
+        L.ora_solid_steps.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_double, P, P]
         L.ora_phi.restype = C.c_double
         L.ora_phi.argtypes = [C.c_double]
         L.ora_lattice.argtypes = [P, P]
@@ -302,3 +303,10 @@ class Oracle:
 
     def step(self, n=1):
         lib().ora_step(self._h, int(n))
+
+    def solid_steps(self, n, dt, gamma, mass, f_ext=None, v=None):
+        """Solid-only velocity-Verlet steps; returns the velocities [3][M]."""
+        v = np.zeros((3, self.M)) if v is None else _f64(v).copy()
+        fe = None if f_ext is None else _f64(f_ext)
+        lib().ora_solid_steps(self._h, int(n), float(dt), float(gamma), float(mass), _p(fe), _p(v))
+        return v

@@ -861,6 +861,31 @@ void ora_stage_forces(ora_t* o) {
   }
 }
 
+/* Solid-only dynamics (the membrane stretching validation of Sec. 3.2): the
+ * markers move under their bodies' forces, the Morse term and an external
+ * force f_ext [3][M], with mass m per marker and viscous damping gamma, by
+ * velocity Verlet (the damping taken half explicitly in the first half-kick
+ * and half implicitly in the second):
+ *   v' = v + dt/2 (F(X)/m - gamma v);  X += dt v';
+ *   v  = (v' + dt/2 F(X)/m) / (1 + gamma dt/2).
+ * v [3][M] is kept by the caller (zero to start from rest). No fluid. */
+void ora_solid_steps(ora_t* o, int64_t n, double dt, double gamma, double mass, const double* f_ext, double* v) {
+  const int64_t M = o->M;
+  for (int64_t s = 0; s < n; ++s) {
+    ora_stage_forces(o);
+    for (int64_t i = 0; i < 3 * M; ++i) {
+      const double F = o->F[i] + (f_ext ? f_ext[i] : 0.0);
+      v[i] += 0.5 * dt * (F / mass - gamma * v[i]);
+      o->X[i] += dt * v[i];
+    }
+    ora_stage_forces(o);
+    for (int64_t i = 0; i < 3 * M; ++i) {
+      const double F = o->F[i] + (f_ext ? f_ext[i] : 0.0);
+      v[i] = (v[i] + 0.5 * dt * F / mass) / (1.0 + 0.5 * gamma * dt);
+    }
+  }
+}
+
 void ora_step(ora_t* o, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     ora_stage_forces(o);

@@ -80,6 +80,9 @@ void ora_stage_spread(ora_t* o);          /* Eq. ibmForceSpread */
 void ora_stage_collide_stream(ora_t* o);  /* Eq. lbm with BGK and Guo forcing */
 void ora_stage_interpolate(ora_t* o);     /* Eq. ibmVelocityInterpret, then X += U */
 void ora_step(ora_t* o, int64_t n);
+/* Solid-only velocity-Verlet steps with viscous damping (membrane
+ * stretching validation, Sec. 3.2); v [3][M] in/out, f_ext [3][M] or NULL. */
+void ora_solid_steps(ora_t* o, int64_t n, double dt, double gamma, double mass, const double* f_ext, double* v);
 
 /* Pure helpers, exported for the pins. */
 double ora_phi(double r);                                        /* Eq. deltaPhiSimple */
