@@ -168,6 +168,18 @@ int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
 int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
                         const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
 
+/* Solid-only dynamics, without the fluid (the membrane stretching
+ * validation of Sec. 3.2): n_steps of velocity Verlet with viscous damping
+ * for every marker, under its body's force (membranes, filaments), the
+ * Morse term when set, and the external force f_ext (host [3][M], may be
+ * NULL), with mass `mass` per marker:
+ *   v' = v + dt/2 (F(X)/m - gamma v);  X += dt v';  v = (v' + dt/2 F(X)/m) / (1 + gamma dt/2).
+ * Marker velocities persist across calls and start from rest after
+ * set_markers. The lattice is untouched. Errors: E_ARG (dt <= 0, gamma < 0,
+ * mass <= 0, n_steps < 0), E_STATE (rigid bodies present: they need the
+ * fluid), E_NOMEM. Waits for the GPU. */
+int ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext);
+
 /* Morse excluded volume (Eq. morsePotential, Sec. 2.2) between markers of
  * different membrane or filament bodies: U = D0 (e^{-2 alpha (r - r0)} -
  * 2 e^{-alpha (r - r0)}) for r < rc, added to the marker forces after the

@@ -92,6 +92,7 @@ def load():
         'ibm_lbm_get_populations': ([P, P], C.c_int),
         'ibm_lbm_set_markers': ([P, C.POINTER(Mesh), I32, P, I64, P], C.c_int),
         'ibm_lbm_set_morse': ([P, D, D, D, D], C.c_int),
+        'ibm_lbm_solid_steps': ([P, I64, D, D, D, P], C.c_int),
         'ibm_lbm_step': ([P, I64], C.c_int),
         'ibm_lbm_step_async': ([P, I64], C.c_int),
         'ibm_lbm_synchronize': ([P], C.c_int),
@@ -190,6 +191,11 @@ def ibm_lbm_set_markers(h, mesh: Mesh | None, bodies, X):
 
 def ibm_lbm_set_morse(h, D0, alpha, r0, rc):
     return _check(h, load().ibm_lbm_set_morse(h, float(D0), float(alpha), float(r0), float(rc)))
+
+
+def ibm_lbm_solid_steps(h, n, dt, gamma, mass, f_ext=None):
+    fe = None if f_ext is None else _f64(f_ext)
+    return _check(h, load().ibm_lbm_solid_steps(h, int(n), float(dt), float(gamma), float(mass), _p(fe)))
 
 
 def ibm_lbm_step(h, n):
@@ -453,6 +459,10 @@ class Simulation:
 
     def set_morse(self, D0, alpha, r0, rc):
         ibm_lbm_set_morse(self.h, D0, alpha, r0, rc)
+
+    def solid_steps(self, n, dt, gamma, mass, f_ext=None):
+        """Solid-only damped velocity-Verlet steps of the markers (no fluid)."""
+        ibm_lbm_solid_steps(self.h, n, dt, gamma, mass, f_ext)
 
     def set_marker_forces(self, F):
         ibm_lbm_set_marker_forces(self.h, F)

@@ -604,6 +604,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   h->m = MarkersDev{};
   h->morse_ready = false;
   h->owner = nullptr;
+  h->solid_v = nullptr;
   h->filament_list = nullptr;
   h->n_filaments = 0;
   h->n_bodies = 0;
@@ -797,6 +798,40 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   }
   h->need_zero_F = covered < n_markers;
   if (h->morse_rc > 0.0) return prepare_morse(h);
+  return IBM_LBM_OK;
+}
+
+int ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext) {
+  if (!h) return IBM_LBM_E_ARG;
+  if (n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0) || !(mass > 0.0))
+    return fail(h, IBM_LBM_E_ARG, "solid_steps: needs n_steps >= 0, dt > 0, gamma >= 0, mass > 0");
+  if (h->n_rigids > 0) return fail(h, IBM_LBM_E_STATE, "solid_steps: rigid bodies need the fluid");
+  const size_t M = (size_t)h->m.M;
+  if (M == 0 || n_steps == 0) return IBM_LBM_OK;
+  cudaStream_t st = h->stream;
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (!h->solid_v) {
+    h->solid_v = (double*)dalloc(h, h->marker_mem, sizeof(double) * 3 * M);
+    if (!h->solid_v) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+    CUDA_TRY(h, cudaMemset(h->solid_v, 0, sizeof(double) * 3 * M));
+  }
+  std::vector<Alloc> tmp;
+  double* fe = nullptr;
+  if (f_ext) {
+    fe = (double*)dalloc(h, tmp, sizeof(double) * 3 * M);
+    if (!fe) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+    CUDA_TRY(h, cudaMemcpy(fe, f_ext, sizeof(double) * 3 * M, cudaMemcpyHostToDevice));
+  }
+  for (int64_t s = 0; s < n_steps; ++s) {
+    enqueue_forces(h, st);
+    launch_solid_half(h->m, h->solid_v, fe, dt, gamma, mass, true, st);
+    enqueue_forces(h, st);
+    launch_solid_half(h->m, h->solid_v, fe, dt, gamma, mass, false, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release_pool(h, tmp);
+  if (e != cudaSuccess) return fail(h, IBM_LBM_E_CUDA, std::string("solid_steps: ") + cudaGetErrorString(e));
   return IBM_LBM_OK;
 }
 

@@ -52,6 +52,7 @@ struct ibm_lbm {
   int* filament_list = nullptr;
   int n_membranes = 0, n_rigids = 0, n_filaments = 0;
   int* owner = nullptr;           // [M] body of each membrane / filament marker, -1 otherwise
+  double* solid_v = nullptr;      // [3][M] marker velocities of the solid-only dynamics (lazily allocated)
   // Morse excluded volume (off while rc <= 0)
   double morse_D0 = 0.0, morse_alpha = 0.0, morse_r0 = 0.0, morse_rc = 0.0;
   ibm::MorseDev morse{};

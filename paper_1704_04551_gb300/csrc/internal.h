@@ -30,6 +30,10 @@ size_t membrane_work_floats(int nv, int nt, int ne);
 cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem);
 void launch_filaments(const MarkersDev& m, const BodyDev* bodies, const int* list, int n, cudaStream_t st);
 
+// solid.cu
+void launch_solid_half(const MarkersDev& m, double* v, const double* fext, double dt, double gamma, double mass,
+                       bool first, cudaStream_t st);
+
 // morse.cu
 void launch_morse(const MorseDev& P, const MarkersDev& m, int nx, int ny, int nz, int geometry, cudaStream_t st);
 int morse_scan_tiles(int n_bins);
