@@ -36,14 +36,14 @@ constexpr int COLLIDE_THREADS = 128;
 // The grid is one-dimensional (a row count above 65535 blocks does not fit
 // the y dimension): block b covers x chunk b % nxb of row block b / nxb,
 // x chunks of a row consecutive.
-template <int S, int ODD, int GEOM, bool DENSE>
+template <int S, int ODD, int GEOM, bool DENSE, bool IDX32>
 __global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
                                                                 int n_rows, int nxb) {
   const int rb = blockIdx.x / nxb, xb = blockIdx.x - rb * nxb;
   const int r = rb * blockDim.y + threadIdx.y;
   const int x = xb * blockDim.x + threadIdx.x;
   if (r >= n_rows || x >= L.nx) return;
-  collide_cell<S, ODD, GEOM, DENSE>(L, rows[r], x);
+  collide_cell<S, ODD, GEOM, DENSE, IDX32>(L, rows[r], x);
 }
 
 // Equilibrium initialisation from the moments in uw (ux, uy, uz, rho - 1).
@@ -188,12 +188,17 @@ void launch_collide_g(const LatticeDev& L, const RowInfo* rows, int n_rows, bool
   const int ty = COLLIDE_THREADS / tx;
   const int nxb = (L.nx + tx - 1) / tx;
   const dim3 block(tx, ty), grid((unsigned)nxb * (unsigned)((n_rows + ty - 1) / ty));
-  if (odd) {
-    if (dense) k_collide<S, 1, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
-    else k_collide<S, 1, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+  // 32-bit element offsets in the odd step while 19 N < 2^32
+  const bool idx32 = (unsigned long long)Q * (unsigned long long)L.N < (1ull << 32);
+  if (odd && idx32) {
+    if (dense) k_collide<S, 1, GEOM, true, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    else k_collide<S, 1, GEOM, false, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+  } else if (odd) {
+    if (dense) k_collide<S, 1, GEOM, true, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    else k_collide<S, 1, GEOM, false, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
   } else {
-    if (dense) k_collide<S, 0, GEOM, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
-    else k_collide<S, 0, GEOM, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    if (dense) k_collide<S, 0, GEOM, true, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
+    else k_collide<S, 0, GEOM, false, false><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
   }
 }
 template <int S>

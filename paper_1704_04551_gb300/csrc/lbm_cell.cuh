@@ -85,7 +85,10 @@ __device__ __forceinline__ bool nb_solid(const Cell& c, int i, int s) {
 using namespace lbm_detail;
 
 // One fluid cell of the fused collide-stream-force step (x in the row R).
-template <int S, int ODD, int GEOM, bool DENSE>
+// IDX32: element offsets of the neighbour-addressed (odd) step computed in
+// 32 bits, valid while 19 N < 2^32 (fewer integer instructions than 64-bit
+// address arithmetic per population; the odd step is issue-bound).
+template <int S, int ODD, int GEOM, bool DENSE, bool IDX32 = false>
 __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo& R, int x) {
   using P = Pop<S>;
   using T = typename P::T;
@@ -104,13 +107,18 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
   // A[x][j] if x - c_j is solid). In both parities f*_i(x) goes back to the
   // slot that held f_opp(i)(x), which covers streaming and half-way
   // bounce-back alike.
+  // element offset of population j at cell e (32- or 64-bit arithmetic)
+  auto elem = [&](int j, int e) -> const T* {
+    if constexpr (IDX32) return A + (unsigned)((unsigned)j * (unsigned)N + (unsigned)e);
+    else return A + (size_t)j * N + e;
+  };
   float d[Q];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
     if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1)))
-      d[j] = P::ld(A + (size_t)j * N + idx, j);
+      d[j] = P::ld(elem(j, idx), j);
     else
-      d[j] = P::ld(A + (size_t)opp(j) * N + (idx + nb_off(c, j, -1)), opp(j));
+      d[j] = P::ld(elem(opp(j), idx + nb_off(c, j, -1)), opp(j));
   }
 
   // moments (Eq. rho_u): rho = sum f, rho u = sum f c + g/2
@@ -176,9 +184,9 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
       v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
     }
     if (!ODD || i == 0 || sol)
-      P::st(A + (size_t)opp(i) * N + widx, opp(i), v);
+      P::st(const_cast<T*>(elem(opp(i), widx)), opp(i), v);
     else
-      P::st(A + (size_t)i * N + (widx + nb_off(c, i, +1)), i, v);
+      P::st(const_cast<T*>(elem(i, widx + nb_off(c, i, +1))), i, v);
   }
 }
 

@@ -158,8 +158,9 @@ __global__ void __launch_bounds__(SERVE_COLLIDE_TX * SERVE_COLLIDE_TY, 6)
   if (!C.active || x >= C.L.nx) return;
   const LatticeDev L = case_lattice(C);
   const RowInfo R = C.rows[it.i];
-  if (C.dense) collide_cell<STORE_F32, ODD, GEOM, true>(L, R, x);
-  else collide_cell<STORE_F32, ODD, GEOM, false>(L, R, x);
+  // served lattices are far below 2^32 / 19 cells (checked at submission)
+  if (C.dense) collide_cell<STORE_F32, ODD, GEOM, true, ODD == 1>(L, R, x);
+  else collide_cell<STORE_F32, ODD, GEOM, false, ODD == 1>(L, R, x);
 }
 
 }  // namespace
@@ -518,7 +519,7 @@ int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t*
   if (!s || !in || !id) return sfail(s, IBM_LBM_E_ARG, "submit: null argument");
   const ibm_lbm_config& L = in->lattice;
   if (L.storage != IBM_LBM_STORE_F32) return sfail(s, IBM_LBM_E_ARG, "submit: served cases use FP32 storage");
-  if (L.nx < 4 || L.ny < 4 || L.nz < 4 || (long long)L.nx * L.ny * L.nz >= (1LL << 31) || in->n_steps < 0 ||
+  if (L.nx < 4 || L.ny < 4 || L.nz < 4 || 19LL * L.nx * L.ny * L.nz >= (1LL << 32) || in->n_steps < 0 ||
       in->n_markers < 0 || (in->n_markers > 0 && !in->X) || in->n_bodies < 0 || (in->n_bodies > 0 && !in->bodies))
     return sfail(s, IBM_LBM_E_ARG, "submit: invalid case");
   auto c = std::make_unique<ibm_lbm_server::Case>();
