@@ -117,3 +117,22 @@ def test_coupled_cells_and_filaments_match_oracle(cuda_lib):
     Xo, _, Fo = ora.markers()
     assert np.abs(Xg - Xo).max() < 1e-5
     assert np.abs(Fg - Fo).max() < 1e-3 * np.abs(Fo).max()
+
+
+def test_morse_and_filament_errors(cuda_lib):
+    from paper_1704_04551_gb300.binding import E_ARG, IbmLbmError, Simulation
+    lat = dict(nx=16, ny=8, nz=8, tau=1.0, geometry=0)
+    sim = Simulation(lat)
+    sim.set_lattice()
+    with pytest.raises(IbmLbmError) as e:
+        sim.set_morse(1e-3, 0.0, 1.0, 1.0)  # alpha must be positive
+    assert e.value.code == E_ARG
+    sim.set_morse(1e-3, 0.5, 1.0, 0.0)  # rc <= 0: switched off
+    X, b = I.filament(0, 1, [3.0, 3.0, 3.0], [1, 0, 0], l0=1.0)
+    with pytest.raises(IbmLbmError) as e:
+        sim.set_markers(None, [b], X)  # a filament needs two beads
+    assert e.value.code == E_ARG
+    X, b = I.filament(0, 4, [3.0, 3.0, 3.0], [1, 0, 0], l0=1.0)
+    with pytest.raises(IbmLbmError) as e:
+        sim.set_markers(None, [dict(b, l0=0.0)], X)  # and a positive rest length
+    assert e.value.code == E_ARG
