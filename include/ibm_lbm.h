@@ -217,13 +217,15 @@ int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies);
 int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]);
 
 /* Stage-by-stage execution for verification: runs one stage of the step
- * (IBM_LBM_STAGE_*) on the handle's stream and waits. COLLIDE writes the
- * moments of every fluid cell; INTERP completes the step. */
+ * (IBM_LBM_STAGE_*) on the handle's stream and waits. SPREAD adds into the
+ * force density, COLLIDE consumes it and writes the moments of every fluid
+ * cell, INTERP clears the force density it consumed and completes the step. */
 int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage);
 /* Overwrite the marker forces (host [3][M]) read by the next SPREAD stage. */
 int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F);
 /* The spread force density waiting for the next COLLIDE (excluding the
- * uniform body force), host [3][N]. */
+ * uniform body force), host [3][N]; zero after an INTERP stage or a full
+ * step. */
 int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
 
 /* Per-stage timing with CUDA events on the handle's stream (measurement

@@ -69,15 +69,11 @@ void drop_graphs(ibm_lbm_t* h) {
 
 int tiles(const LatticeDev& L) { return L.ntx * L.nty * L.ntz; }
 
-// Lattice view for a step of the given AA parity: that step spreads into and
-// reads gbuf[odd] / fbuf[odd] and clears gbuf[!odd] where fbuf[!odd] is set.
+// Lattice view for a step (the AA parity is a kernel template argument, the
+// force density and its flags are single buffers).
 LatticeDev lat(const ibm_lbm_t* h, bool odd) {
-  LatticeDev L = h->L;
-  L.g = h->gbuf[odd ? 1 : 0];
-  L.flags = h->fbuf[odd ? 1 : 0];
-  L.g_next = h->gbuf[odd ? 0 : 1];
-  L.flags_next = h->fbuf[odd ? 0 : 1];
-  return L;
+  (void)odd;
+  return h->L;
 }
 
 // Marker forces: each body's own forces (membranes, rigid tethers,
@@ -477,14 +473,14 @@ int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, vo
   const size_t sp = cfg->storage == STORE_F32 ? 4 : 2;
   L.pop = dalloc(h, h->lattice_mem, (size_t)Q * N * sp);
   L.uw = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
-  for (int p = 0; p < 2; ++p) {
-    h->gbuf[p] = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
-    h->fbuf[p] = (uint8_t*)dalloc(h, h->lattice_mem, (size_t)tiles(L));
-  }
+  h->gbuf = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * N);
+  h->fbuf = (uint8_t*)dalloc(h, h->lattice_mem, (size_t)tiles(L));
+  L.g = h->gbuf;  // every view of the lattice (steps, stages, server) carries them
+  L.flags = h->fbuf;
   L.status = (int*)dalloc(h, h->lattice_mem, 256);
   h->d_diag = (double*)dalloc(h, h->lattice_mem, 8 * sizeof(double));
   h->d_umax = (unsigned*)dalloc(h, h->lattice_mem, 256);
-  if (!L.pop || !L.uw || !h->gbuf[0] || !h->gbuf[1] || !h->fbuf[0] || !h->fbuf[1] || !L.status || !h->d_diag ||
+  if (!L.pop || !L.uw || !h->gbuf || !h->fbuf || !L.status || !h->d_diag ||
       !h->d_umax) {
     h->err = "device allocation failed";
     return bail(IBM_LBM_E_NOMEM);
@@ -540,10 +536,8 @@ int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
   CUDA_TRY(h, cudaMemcpyAsync(L.uw, m.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, h->stream));
   launch_init_equilibrium(L, h->cfg.storage, h->stream);
   CUDA_TRY(h, cudaGetLastError());
-  for (int p = 0; p < 2; ++p) {
-    CUDA_TRY(h, cudaMemsetAsync(h->gbuf[p], 0, sizeof(float4) * N, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->fbuf[p], 0, (size_t)tiles(L), h->stream));
-  }
+  CUDA_TRY(h, cudaMemsetAsync(h->gbuf, 0, sizeof(float4) * N, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->fbuf, 0, (size_t)tiles(L), h->stream));
   CUDA_TRY(h, cudaMemsetAsync(L.status, 0, sizeof(int), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->steps = 0;
@@ -565,11 +559,9 @@ int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
   }
   release_pool(h, tmp);
   if (rc) return fail(h, rc, "set_populations: CUDA error");
-  // the parity restarts: clear both force-density buffers and their flags
-  for (int p = 0; p < 2; ++p) {
-    CUDA_TRY(h, cudaMemsetAsync(h->gbuf[p], 0, sizeof(float4) * (size_t)h->L.N, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->fbuf[p], 0, (size_t)tiles(h->L), h->stream));
-  }
+  // the parity restarts: clear the force density and its flags
+  CUDA_TRY(h, cudaMemsetAsync(h->gbuf, 0, sizeof(float4) * (size_t)h->L.N, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->fbuf, 0, (size_t)tiles(h->L), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->odd_next = false;
   return IBM_LBM_OK;
@@ -795,6 +787,9 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     if ((rc = upload<MarkerGroup>(h, h->marker_mem, &h->groups, groups.data(), groups.size()))) return rc;
     h->boxes = (int4*)dalloc(h, h->marker_mem, sizeof(int4) * 2 * std::max<size_t>(1, groups.size()));
     if (!h->boxes) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+    // no box until the first spreading: an interpolation run before it (the
+    // stage interface allows that) takes the per-marker path
+    CUDA_TRY(h, cudaMemset(h->boxes, 0, sizeof(int4) * 2 * std::max<size_t>(1, groups.size())));
   }
   h->need_zero_F = covered < n_markers;
   if (h->morse_rc > 0.0) return prepare_morse(h);
@@ -912,7 +907,7 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
   const size_t N = (size_t)h->L.N;
   std::vector<float4> tmp(N);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpy(tmp.data(), h->gbuf[h->odd_next ? 1 : 0], sizeof(float4) * N, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(tmp.data(), h->gbuf, sizeof(float4) * N, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < N; ++i) {
     g[i] = tmp[i].x; g[N + i] = tmp[i].y; g[2 * N + i] = tmp[i].z;
   }

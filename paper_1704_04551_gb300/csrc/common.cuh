@@ -54,15 +54,14 @@ struct LatticeDev {
   int ntx, nty, ntz;     // tile grid
   void* pop;             // [19][N] in the storage type
   float4* uw;            // moments of the last collision: (ux, uy, uz, rho - 1) [N]
-  // Force density and touched-tile flags are double-buffered by step parity:
-  // this step spreads into g / flags and the collision reads them; the
-  // collision also clears g_next where flags_next (the previous step's tiles)
-  // is set, so that buffer starts the next step at zero. Reading and clearing
-  // the same words in one pass is avoided on purpose.
+  // Force density and touched-tile flags: the step's spreading adds into g
+  // (zero at that point) and marks flags, the collision reads g where flags
+  // is set, and the interpolation, which sweeps the same boxes of cells
+  // afterwards, writes g back to zero there (in its latency-bound box load,
+  // not in the bandwidth-bound collision). flags is cleared at the start of
+  // each step.
   float4* g;             // spread force density (gx, gy, gz, 0) [N]
   uint8_t* flags;        // [ntx*nty*ntz]: tile touched by a marker stencil this step
-  float4* g_next;        // the other buffer, cleared where flags_next is set
-  const uint8_t* flags_next;
   int* status;           // device status word (0 = OK)
 };
 

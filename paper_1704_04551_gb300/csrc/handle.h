@@ -34,9 +34,9 @@ struct ibm_lbm {
   bool has_alloc = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  LatticeDev L{};                 // g / flags fields unused: see lat()
-  float4* gbuf[2] = {nullptr, nullptr};   // force density, by step parity
-  uint8_t* fbuf[2] = {nullptr, nullptr};  // touched-tile flags, by step parity
+  LatticeDev L{};                 // the lattice view every kernel receives
+  float4* gbuf = nullptr;         // force density
+  uint8_t* fbuf = nullptr;        // touched-tile flags
   RowInfo* rows = nullptr;        // fluid rows of the lattice
   int n_rows = 0;
   std::vector<Alloc> lattice_mem, marker_mem;

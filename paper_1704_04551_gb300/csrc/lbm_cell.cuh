@@ -137,7 +137,6 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
     const float4 gg = L.g[idx];
     Gx += gg.x; Gy += gg.y; Gz += gg.z;
   }
-  if (L.flags_next[tile]) L.g_next[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
   const float rho = 1.0f + drho;
   const float irho = 1.0f / rho;
   const float ux = (jx + 0.5f * Gx) * irho;

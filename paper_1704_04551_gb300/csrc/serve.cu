@@ -42,8 +42,8 @@ namespace {
 
 struct CaseDev {
   LatticeDev L;  // g / flags are taken from gbuf / fbuf by parity
-  float4* gbuf[2];
-  uint8_t* fbuf[2];
+  float4* gbuf;
+  uint8_t* fbuf;
   const RowInfo* rows;
   MarkersDev m;
   const MarkerGroup* groups;
@@ -61,10 +61,8 @@ struct Item {
 
 __device__ __forceinline__ LatticeDev case_lattice(const CaseDev& C) {
   LatticeDev L = C.L;
-  L.g = C.gbuf[C.odd];
-  L.flags = C.fbuf[C.odd];
-  L.g_next = C.gbuf[1 - C.odd];
-  L.flags_next = C.fbuf[1 - C.odd];
+  L.g = C.gbuf;
+  L.flags = C.fbuf;
   return L;
 }
 
@@ -91,7 +89,7 @@ __global__ void k_book_end(CaseDev* cases, int n) {
 __global__ void k_clear_flags(const CaseDev* cases) {
   const CaseDev& C = cases[blockIdx.x];
   if (!C.active) return;
-  uint8_t* f = C.fbuf[C.odd];
+  uint8_t* f = C.fbuf;
   for (int i = threadIdx.x; i < C.ntiles; i += blockDim.x) f[i] = 0;
   if (C.zero_F)
     for (int k = threadIdx.x; k < C.m.M; k += blockDim.x) C.m.F[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -328,8 +326,8 @@ int rebuild(ibm_lbm_server_t* s) {
     ibm_lbm_t* h = s->running[i]->h;
     CaseDev& C = s->h_cases[i];
     C.L = h->L;
-    C.gbuf[0] = h->gbuf[0]; C.gbuf[1] = h->gbuf[1];
-    C.fbuf[0] = h->fbuf[0]; C.fbuf[1] = h->fbuf[1];
+    C.gbuf = h->gbuf;
+    C.fbuf = h->fbuf;
     C.rows = h->rows;
     C.m = h->m;
     C.groups = h->groups;

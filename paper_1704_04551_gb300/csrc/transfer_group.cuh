@@ -364,7 +364,11 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
           const int r = r0 + q * rstep;
           u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
           int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
-          if (r < nrows && fluid_row<GEOM>(L, y, z)) u[q] = L.uw[(size_t)L.nx * (y + L.ny * z) + x];
+          if (r < nrows && fluid_row<GEOM>(L, y, z)) {
+            const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
+            u[q] = L.uw[gi];
+            L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed by this step's collision
+          }
         }
 #pragma unroll
         for (int q = 0; q < RIF; ++q) {
@@ -410,6 +414,7 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
           if (!fluid_row<GEOM>(L, y, z)) continue;
           const float w = s.wy[b] * s.wz[c];
           const float4 u = L.uw[L.nx * (y + L.ny * z) + x];
+          L.g[L.nx * (y + L.ny * z) + x] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed by the collision
           ux = fmaf(w, u.x, ux);
           uy = fmaf(w, u.y, uy);
           uz = fmaf(w, u.z, uz);
