@@ -209,7 +209,7 @@ int enqueue_steps(ibm_lbm_t* h, int64_t n) {
 struct HostMesh {
   std::vector<int4> edges;
   std::vector<int2> edge_tris;
-  std::vector<float2> edge_rest;
+  std::vector<float4> edge_rest;
   std::vector<int> v_edge_start, v_edge, v_tri_start, v_tri;
   std::vector<int4> tris;
   std::vector<float> area0;
@@ -274,7 +274,7 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
     V3 n1 = crs(ev, sub(c, a)), n2 = crs(sub(a, b), sub(d, b));
     const double L = std::sqrt(dt3(ev, ev));
     const double th = std::atan2(dt3(crs(n1, n2), ev) / L, dt3(n1, n2));
-    out.edge_rest[i] = make_float2((float)L, (float)th);
+    out.edge_rest[i] = make_float4((float)L, (float)std::cos(th), (float)std::sin(th), 0.f);
   }
   out.area0.resize(nt);
   out.A0 = out.V0 = 0;
@@ -736,7 +736,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     MeshDev& D = h->mesh;
     D.off_edges = section(e16.data(), e16.size() * sizeof(ushort4));
     D.off_edge_tris = section(et16.data(), et16.size() * sizeof(ushort2));
-    D.off_edge_rest = section(hm.edge_rest.data(), hm.edge_rest.size() * sizeof(float2));
+    D.off_edge_rest = section(hm.edge_rest.data(), hm.edge_rest.size() * sizeof(float4));
     D.off_tris = section(t16.data(), t16.size() * sizeof(ushort4));
     D.off_area0 = section(hm.area0.data(), hm.area0.size() * sizeof(float));
     D.off_ve_start = section(ves.data(), ves.size() * 2);

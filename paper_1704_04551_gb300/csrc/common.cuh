@@ -159,7 +159,7 @@ struct MeshDev {
   // Template topology packed in one buffer of 16-byte-aligned sections:
   // edges ushort4 (a, b, c, d): edge a->b, wing c in the triangle with a->b,
   // d in the other; edge_tris ushort2 (t1, t2): those two triangles;
-  // edge_rest float2 (l0, theta0); tris ushort4 (v0, v1, v2, -); area0 float;
+  // edge_rest float4 (l0, cos theta0, sin theta0, -); tris ushort4 (v0, v1, v2, -); area0 float;
   // per-vertex CSR lists ve_start/ve of (edge << 2 | role a,b,c,d) and
   // vt_start/vt of (triangle << 2 | slot), all unsigned short.
   const unsigned char* packed;

@@ -57,7 +57,7 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 struct Topo {
   const ushort4* edges;      // (a, b, c, d)
   const ushort2* edge_tris;  // (t1, t2)
-  const float2* edge_rest;   // (l0, theta0)
+  const float4* edge_rest;   // (l0, cos theta0, sin theta0, -)
   const ushort4* tris;       // (v0, v1, v2, -)
   const float* area0;
 };
@@ -66,7 +66,7 @@ __device__ __forceinline__ Topo topo_at(const unsigned char* base, const MeshDev
   Topo T;
   T.edges = reinterpret_cast<const ushort4*>(base + mesh.off_edges);
   T.edge_tris = reinterpret_cast<const ushort2*>(base + mesh.off_edge_tris);
-  T.edge_rest = reinterpret_cast<const float2*>(base + mesh.off_edge_rest);
+  T.edge_rest = reinterpret_cast<const float4*>(base + mesh.off_edge_rest);
   T.tris = reinterpret_cast<const ushort4*>(base + mesh.off_tris);
   T.area0 = reinterpret_cast<const float*>(base + mesh.off_area0);
   return T;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   auto pass_b = [&](auto&& add) {
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
       const ushort4 E = T.edges[e];
-      const float2 rest = T.edge_rest[e];
+      const float4 rest = T.edge_rest[e];
       const float3 ev = dv(E.y, E.x);  // b - a
       const float L2 = dot(ev, ev), l = sqrtf(L2);
       const float l0 = rest.x, x = l / (2.0f * l0);
@@ -181,8 +181,11 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
       const ushort2 ET = T.edge_tris[e];
       const float3 n1 = normal(ET.x), n2 = normal(ET.y);
-      const float theta = atan2f(dot(cross(n1, n2), ev) / l, dot(n1, n2));
-      const float sb = k_b * sinf(theta - rest.y);
+      // sin(theta - theta0) = sin(theta) cos(theta0) - cos(theta) sin(theta0), with
+      // cos(theta), sin(theta) from the normals (no inverse trigonometry)
+      const float inv = rsqrtf(dot(n1, n1) * dot(n2, n2));
+      const float cth = dot(n1, n2) * inv, sth = dot(cross(n1, n2), ev) / l * inv;
+      const float sb = k_b * (sth * rest.y - cth * rest.z);
       const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
       const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
       add(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
