@@ -162,9 +162,24 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   // contribution handed to `add`
   float qmax = 0.f;  // largest contribution component seen by this thread
   auto pass_b = [&](auto&& add) {
+    // the next edge's topology is loaded while this one is computed
+    ushort4 En = make_ushort4(0, 0, 0, 0);
+    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+    ushort2 ETn = make_ushort2(0, 0);
+    if ((int)threadIdx.x < ne) {
+      En = T.edges[threadIdx.x];
+      rn = T.edge_rest[threadIdx.x];
+      ETn = T.edge_tris[threadIdx.x];
+    }
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-      const ushort4 E = T.edges[e];
-      const float4 rest = T.edge_rest[e];
+      const ushort4 E = En;
+      const float4 rest = rn;
+      const ushort2 ET = ETn;
+      if (e + (int)blockDim.x < ne) {
+        En = T.edges[e + blockDim.x];
+        rn = T.edge_rest[e + blockDim.x];
+        ETn = T.edge_tris[e + blockDim.x];
+      }
       const float3 ev = dv(E.y, E.x);  // b - a
       const float L2 = dot(ev, ev), l = sqrtf(L2);
       const float l0 = rest.x, x = l / (2.0f * l0);
@@ -179,7 +194,6 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       // bending: F_v = -s dtheta/dv with dtheta/dc = -L n1/|n1|^2,
       // dtheta/dd = -L n2/|n2|^2, dtheta/da = -(1-t1) g_c - (1-t2) g_d,
       // dtheta/db = -t1 g_c - t2 g_d, t1,2 = (c,d - a).(b - a)/L^2
-      const ushort2 ET = T.edge_tris[e];
       const float3 n1 = normal(ET.x), n2 = normal(ET.y);
       // sin(theta - theta0) = sin(theta) cos(theta0) - cos(theta) sin(theta0), with
       // cos(theta), sin(theta) from the normals (no inverse trigonometry)
@@ -193,11 +207,22 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       add(E.z, (-sb) * gc);
       add(E.w, (-sb) * gd);
     }
+    ushort4 Trn = make_ushort4(0, 0, 0, 0);
+    float A0n = 1.f;
+    if ((int)threadIdx.x < nt) {
+      Trn = T.tris[threadIdx.x];
+      A0n = T.area0[threadIdx.x];
+    }
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      const ushort4 Tr = T.tris[t];
+      const ushort4 Tr = Trn;
+      const float At0 = A0n;
+      if (t + (int)blockDim.x < nt) {
+        Trn = T.tris[t + blockDim.x];
+        A0n = T.area0[t + blockDim.x];
+      }
       const int vv[3] = {Tr.x, Tr.y, Tr.z};
       const float3 N = normal(t);
-      const float At = sA[t], At0 = T.area0[t];
+      const float At = sA[t];
       const float coef = k_l * (At - At0) / At0 + cg;
       const float3 nh = (1.0f / (2.0f * At)) * N;
       const float3 fV = (-cv / 6.0f) * N;

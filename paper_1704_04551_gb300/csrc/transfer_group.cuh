@@ -53,15 +53,28 @@ struct LaneStencil {
   float wx;           // weight of node bx + a
   float wy[4], wz[4];
 };
-__device__ __forceinline__ void lane_stencil(const MarkersDev& m, int k, int a, LaneStencil& s) {
+// The stencil cache of one marker as read from global memory (the
+// interpolation loads the next pass's entries while the current pass
+// gathers, so that a pass does not wait for its own loads).
+struct RawStencil {
+  int c[3];
+  float f[3];
+};
+__device__ __forceinline__ void load_raw(const MarkersDev& m, int k, RawStencil& r) {
   const size_t M = (size_t)m.M;
-  s.bx = m.cell[k] - 1;
-  s.by = m.cell[M + k] - 1;
-  s.bz = m.cell[2 * M + k] - 1;
-  const float fx = m.frac[k], fy = m.frac[M + k], fz = m.frac[2 * M + k];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    r.c[q] = m.cell[q * M + k];
+    r.f[q] = m.frac[q * M + k];
+  }
+}
+__device__ __forceinline__ void lane_stencil(const RawStencil& r, int a, LaneStencil& s) {
+  s.bx = r.c[0] - 1;
+  s.by = r.c[1] - 1;
+  s.bz = r.c[2] - 1;
   // node b + a sits at distance (a - 1) - frac from X
-  s.wx = phi((float)(a - 1) - fx);
-  const float wy_own = phi((float)(a - 1) - fy), wz_own = phi((float)(a - 1) - fz);
+  s.wx = phi((float)(a - 1) - r.f[0]);
+  const float wy_own = phi((float)(a - 1) - r.f[1]), wz_own = phi((float)(a - 1) - r.f[2]);
   const int base = threadIdx.x & 28;  // first lane of this 4-lane group within the warp
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -281,8 +294,10 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
     const int j = j0 + (threadIdx.x >> 2);
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
+    RawStencil r;
+    load_raw(m, k, r);
     LaneStencil s;
-    lane_stencil(m, k, a, s);
+    lane_stencil(r, a, s);
     if (!in_smem) mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active && a == 0);
     if (!active || !any_force) continue;
     const float4 F = m.F[k];
@@ -344,6 +359,14 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
   const size_t M = (size_t)m.M;
   const bool in_smem = dims.w != 0;
   const int vol = dims.x * dims.y * dims.z;
+  const int a = threadIdx.x & 3;
+  const int pass = blockDim.x >> 2;            // markers per pass
+  const int slot = threadIdx.x >> 2;           // this lane's marker within a pass
+  const int wfirst = (threadIdx.x >> 5) << 3;  // first marker of this warp within a pass
+  const bool moves = !(G.flags & GROUP_FIXED);
+  // the first pass's stencil cache is loaded while the velocity box is
+  RawStencil nxt;
+  if (wfirst < G.count) load_raw(m, G.first + (slot < G.count ? slot : 0), nxt);
   if (in_smem) {
     // load the box of velocities row by row; solid rows contribute zero
     // one warp per box row, four rows in flight per lane (the loads are
@@ -383,14 +406,24 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     }
     __syncthreads();
   }
-  const int a = threadIdx.x & 3;
-  for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
-    if (j0 + ((threadIdx.x >> 5) << 3) >= G.count) continue;  // the whole warp is past the group's end
-    const int j = j0 + (threadIdx.x >> 2);
+  // whole warps iterate together (shuffles inside); a warp stops at the
+  // first pass that lies entirely past the group's end
+  for (int j0 = 0; j0 + wfirst < G.count; j0 += pass) {
+    const int j = j0 + slot;
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
+    // this lane's coordinate (advection) and the next pass's stencil cache
+    // are loaded before the gather
+    const size_t off = (size_t)a * M + k;
+    double Xo = 0.0;
+    if (active && moves && a < 3) Xo = m.X[off];
+    const RawStencil cur = nxt;
+    if (j0 + pass + wfirst < G.count) {
+      const int jn = j + pass;
+      load_raw(m, G.first + (jn < G.count ? jn : 0), nxt);
+    }
     LaneStencil s;
-    lane_stencil(m, k, a, s);
+    lane_stencil(cur, a, s);
     float ux = 0.f, uy = 0.f, uz = 0.f;
     if (in_smem) {
       const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
@@ -431,11 +464,10 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     }
     if (!active) continue;
     if (a == 0) m.U[k] = make_float4(ux, uy, uz, 0.f);
-    if (a < 3 && !(G.flags & GROUP_FIXED)) {
+    if (a < 3 && moves) {
       // advection of one coordinate per lane (FP64), then its stencil cache
       const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
-      const size_t off = (size_t)a * M + k;
-      const double Xn = m.X[off] + (double)ua;
+      const double Xn = Xo + (double)ua;
       m.X[off] = Xn;
       cache_coord(m, off, Xn);
     }
