@@ -161,10 +161,11 @@ int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f);
 int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
 
 /* Markers, bodies and (optional) membrane template. mesh may be NULL when
- * no body is a membrane. X: host [3][n_markers]. Markers outside every
- * body are passive tracers (zero force). Errors: E_ARG (overlapping or
- * out-of-range bodies, membrane count != n_vertices, non-manifold mesh,
- * template too large), E_NOMEM. */
+ * no body is a membrane. X: host [3][n_markers], unwrapped coordinates in
+ * lattice units, finite with |X| < 2^30. Markers outside every body are
+ * passive tracers (zero force). Errors: E_ARG (overlapping or out-of-range
+ * bodies, membrane count != n_vertices, non-manifold mesh, template too
+ * large, a non-finite or too large position), E_NOMEM. */
 int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
                         const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
 

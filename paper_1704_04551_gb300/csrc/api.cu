@@ -645,6 +645,10 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
     if (hm.edges.size() >= 16384 || (size_t)mesh->n_triangles >= 16384)
       return fail(h, IBM_LBM_E_ARG, "set_markers: membrane template has too many edges or triangles");
   }
+  // floor(X) of every coordinate must fit the stencil cache's int32
+  for (size_t i = 0; i < 3 * (size_t)M; ++i)
+    if (!(std::fabs(X[i]) < 1073741824.0))
+      return fail(h, IBM_LBM_E_ARG, "set_markers: positions must be finite with |X| < 2^30");
   int rc;
   // marker arrays
   h->m.M = M;

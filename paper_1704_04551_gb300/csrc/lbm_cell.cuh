@@ -36,6 +36,17 @@ struct Pop {
     else if constexpr (S == STORE_F16) *p = __float2half_rn(v * dev_scale(i));
     else *p = __float2bfloat16_rn(v * dev_scale(i));
   }
+  // the stored value itself (K_i d_i for the half-precision formats)
+  __device__ static __forceinline__ float ld_raw(const T* p) {
+    if constexpr (S == STORE_F32) return *p;
+    else if constexpr (S == STORE_F16) return __half2float(*p);
+    else return __bfloat162float(*p);
+  }
+  __device__ static __forceinline__ void st_raw(T* p, float v) {
+    if constexpr (S == STORE_F32) *p = v;
+    else if constexpr (S == STORE_F16) *p = __float2half_rn(v);
+    else *p = __float2bfloat16_rn(v);
+  }
 };
 
 struct Cell {
@@ -112,23 +123,28 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
     if constexpr (IDX32) return A + (unsigned)((unsigned)j * (unsigned)N + (unsigned)e);
     else return A + (size_t)j * N + e;
   };
+  // HALF: d[] holds the stored values K_i d_i of the half-precision formats
+  // (K_i = dev_scale(i), a power of two, so that folding 1/K_i into the
+  // moment sums and K_i into the update constants is exact).
+  constexpr bool HALF = S != STORE_F32;
   float d[Q];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
     if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1)))
-      d[j] = P::ld(elem(j, idx), j);
+      d[j] = P::ld_raw(elem(j, idx));
     else
-      d[j] = P::ld(elem(opp(j), idx + nb_off(c, j, -1)), opp(j));
+      d[j] = P::ld_raw(elem(opp(j), idx + nb_off(c, j, -1)));
   }
 
   // moments (Eq. rho_u): rho = sum f, rho u = sum f c + g/2
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    drho += d[i];
-    if (cx(i)) jx += cx(i) * d[i];
-    if (cy(i)) jy += cy(i) * d[i];
-    if (cz(i)) jz += cz(i) * d[i];
+    const float k = HALF ? 1.0f / dev_scale(i) : 1.0f;
+    drho = fmaf(d[i], k, drho);
+    if (cx(i)) jx = fmaf(d[i], cx(i) * k, jx);
+    if (cy(i)) jy = fmaf(d[i], cy(i) * k, jy);
+    if (cz(i)) jz = fmaf(d[i], cz(i) * k, jz);
   }
   float Gx = L.g0x, Gy = L.g0y, Gz = L.g0z;
   const int tile = R.trow + (x >> TILE_X_SHIFT);
@@ -152,14 +168,39 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
   const float om = L.omega, pre = L.guo_pre;
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
   const float uG = ux * Gx + uy * Gy + uz * Gz;
+  if constexpr (!HALF) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const float w = wgt(i);
-    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-    const float cG = cx(i) * Gx + cy(i) * Gy + cz(i) * Gz;
-    const float deq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
-    const float Fi = pre * w * (3.0f * (cG - uG) + 9.0f * cu * cG);
-    d[i] = d[i] + om * (deq - d[i]) + Fi;
+    for (int i = 0; i < Q; ++i) {
+      const float w = wgt(i);
+      const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+      const float cG = cx(i) * Gx + cy(i) * Gy + cz(i) * Gz;
+      const float deq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
+      const float Fi = pre * w * (3.0f * (cG - uG) + 9.0f * cu * cG);
+      d[i] = d[i] + om * (deq - d[i]) + Fi;
+    }
+  } else {
+    // The same update, regrouped for the half-precision formats (their
+    // rounding dominates the error): with cu = c.u and cG = c.G,
+    //   K_i (om f^eq_i + F_i) = K_i w_i [T0 + cu (3 om rho + 4.5 om rho cu + 9 pre cG) + 3 pre cG],
+    //   T0 = om (drho - rho 1.5 u^2) - 3 pre u.G,
+    // K_i w_i = 8/9 for every moving direction (4/3 at rest), and the pair
+    // i, i+1 = opp(i) shares the even part in cu and flips the odd part.
+    const float om1 = 1.0f - om;
+    const float T0 = om * (drho - rho * usq15) - 3.0f * pre * uG;
+    constexpr float KW = 8.0f / 9.0f;
+    const float A = (KW * 3.0f) * om * rho, B = (KW * 4.5f) * om * rho;
+    const float P3 = (KW * 3.0f) * pre, P9 = (KW * 9.0f) * pre;
+    const float T0w = KW * T0;
+    d[0] = fmaf(om1, d[0], (4.0f / 3.0f) * T0);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+      const float cG = cx(i) * Gx + cy(i) * Gy + cz(i) * Gz;
+      const float even = fmaf(fmaf(B, cu, P9 * cG), cu, T0w);
+      const float odd = fmaf(A, cu, P3 * cG);
+      d[i] = fmaf(om1, d[i], even + odd);
+      d[i + 1] = fmaf(om1, d[i + 1], even - odd);
+    }
   }
 
   // Recompute the write addresses from a few laundered registers instead of
@@ -173,13 +214,14 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
     float v = d[i];
     const bool sol = (GEOM != GEOM_PERIODIC) && i != 0 && nb_solid(c, i, +1);
     if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
+      // stored into slot opp(i): the half-precision scale of that slot
       const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
-      v -= 6.0f * wgt(i) * rho * (float)cx(i) * uw;
+      v -= (HALF ? dev_scale(opp(i)) : 1.0f) * 6.0f * wgt(i) * rho * (float)cx(i) * uw;
     }
     if (!ODD || i == 0 || sol)
-      P::st(const_cast<T*>(elem(opp(i), widx)), opp(i), v);
+      P::st_raw(const_cast<T*>(elem(opp(i), widx)), v);
     else
-      P::st(const_cast<T*>(elem(i, widx + nb_off(c, i, +1))), i, v);
+      P::st_raw(const_cast<T*>(elem(i, widx + nb_off(c, i, +1))), v);
   }
 }
 

@@ -244,8 +244,49 @@ def test_errors_are_reported(cuda_lib):
         sim.set_markers(None, [dict(kind=1, first=0, count=5, mass=1.0, inertia=[1, 1, 1])], np.zeros((3, 3)))
     with pytest.raises(IbmLbmError):
         sim.step(-1)
+    for bad in (np.nan, np.inf, 2.0 ** 30):  # floor(X) must fit an int32
+        X = np.full((3, 4), 5.0)
+        X[1, 2] = bad
+        with pytest.raises(IbmLbmError) as e:
+            sim.set_markers(None, [], X)
+        assert e.value.code == cuda_lib.E_ARG
     sim.set_markers(None, [], np.zeros((3, 0)))
     sim.step(0)
+
+
+def test_positions_round_trip_and_unwrapped_coordinates(cuda_lib):
+    """set/get returns the FP64 positions unchanged, negative and far
+    unwrapped coordinates included; markers moved by whole periods on the
+    periodic lattice spread and interpolate exactly as the unshifted ones
+    (the stencil cache floors negative coordinates correctly)."""
+    lat = LATTICES['periodic']
+    nx, ny, nz = shape(lat)
+    rng = np.random.default_rng(12)
+    X = np.concatenate([rng.uniform(-3e5, 3e5, (3, 50)), rng.uniform(-2, 2, (3, 50)),
+                        np.round(rng.uniform(-100, 100, (3, 20)) * 2.0 ** 32) / 2.0 ** 32], axis=1)
+    sim = cuda_lib.Simulation(lat)
+    sim.set_markers(None, [], X)
+    Xg, _, _ = sim.markers()
+    assert np.array_equal(Xg, X)
+    X0 = np.round(markers_inside(lat, 200, 9) * 2.0 ** 32) / 2.0 ** 32  # so that X0 + shift is exact
+    shift = np.array([-nx, 2 * ny, -3 * nz], dtype=float)[:, None]
+    F = 1e-3 * (2 * rng.random(X0.shape) - 1)
+    rho, u = I.random_fields(shape(lat), 3)
+    out = []
+    for Xs in (X0, X0 + shift):
+        s = cuda_lib.Simulation(lat)
+        s.set_lattice(rho, u)
+        s.set_markers(None, [], Xs)
+        s.set_marker_forces(F)
+        s.stage(cuda_lib.STAGE_SPREAD)
+        g = s.force_density()
+        s.stage(cuda_lib.STAGE_INTERP)
+        Xa, U, _ = s.markers()
+        out.append((g, U, Xa - Xs))
+    (g0, U0, d0), (g1, U1, d1) = out
+    assert np.abs(g1 - g0).max() <= 1e-6 * np.abs(g0).max()  # same sums, another order of float atomics
+    assert np.array_equal(U1, U0)
+    assert np.abs(d1 - d0).max() <= 2.0 ** -32
 
 
 def test_rigid_direct_forcing_stage_and_coupled(cuda_lib):
