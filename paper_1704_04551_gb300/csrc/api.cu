@@ -3,11 +3,14 @@
 // (captured into CUDA graphs: one graph per 16 steps, plus single steps).
 #include <cuda_runtime.h>
 
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -46,6 +49,27 @@ void* dalloc(ibm_lbm_t* h, std::vector<Alloc>& pool, size_t bytes) {
     h->bytes += bytes;
   }
   return p;
+}
+
+// Write one byte per page of a host output buffer from several threads, so
+// that the page faults of a freshly allocated buffer are taken in parallel
+// before a device-to-host copy fills it. The buffer is overwritten anyway.
+void touch_pages(void* p, size_t bytes) {
+  if (!p || bytes < ((size_t)64 << 20)) return;
+  const long pg = sysconf(_SC_PAGESIZE);
+  const size_t page = pg > 0 ? (size_t)pg : 4096;
+  const unsigned nt = std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
+  const size_t chunk = (bytes / nt + page - 1) / page * page;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    const size_t b = t * chunk, e = std::min(bytes, b + chunk);
+    if (b >= e) break;
+    th.emplace_back([p, b, e, page] {
+      volatile char* q = static_cast<volatile char*>(p);
+      for (size_t o = b; o < e; o += page) q[o] = 0;
+    });
+  }
+  for (auto& x : th) x.join();
 }
 
 void release_pool(ibm_lbm_t* h, std::vector<Alloc>& pool) {
@@ -526,14 +550,27 @@ int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
   if (!h) return IBM_LBM_E_ARG;
   LatticeDev& L = h->L;
   const size_t N = (size_t)L.N;
-  std::vector<float4> m(N);
-  for (size_t i = 0; i < N; ++i) {
-    const double r = rho ? rho[i] : 1.0;
-    m[i] = make_float4(u ? (float)u[i] : 0.f, u ? (float)u[N + i] : 0.f, u ? (float)u[2 * N + i] : 0.f,
-                       (float)(r - 1.0));
-  }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(L.uw, m.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, h->stream));
+  // the caller's FP64 arrays go to the device as they are and are converted
+  // there (a host conversion loop over N cells costs more than the copy)
+  std::vector<Alloc> tmp;
+  double* d_rho = rho ? (double*)dalloc(h, tmp, sizeof(double) * N) : nullptr;
+  double* d_u = u ? (double*)dalloc(h, tmp, sizeof(double) * 3 * N) : nullptr;
+  if ((rho && !d_rho) || (u && !d_u)) {
+    release_pool(h, tmp);
+    return fail(h, IBM_LBM_E_NOMEM, "set_lattice: device allocation failed");
+  }
+  int rc = IBM_LBM_OK;
+  if (rho && cudaMemcpyAsync(d_rho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (!rc && u && cudaMemcpyAsync(d_u, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (!rc) {
+    launch_set_moments(L, d_rho, d_u, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IBM_LBM_E_CUDA;
+  }
+  release_pool(h, tmp);
+  if (rc) return fail(h, rc, "set_lattice: CUDA error");
   launch_init_equilibrium(L, h->cfg.storage, h->stream);
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaMemsetAsync(h->gbuf, 0, sizeof(float4) * N, h->stream));
@@ -922,24 +959,29 @@ int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
   if (!h) return IBM_LBM_E_ARG;
   const LatticeDev& L = h->L;
   const size_t N = (size_t)L.N;
-  std::vector<float4> tmp(N);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpy(tmp.data(), L.uw, sizeof(float4) * N, cudaMemcpyDeviceToHost));
-  for (int z = 0; z < L.nz; ++z)
-    for (int y = 0; y < L.ny; ++y) {
-      const bool fl = fluid_yz(L, y, z);
-      const size_t row = (size_t)L.nx * (y + (size_t)L.ny * z);
-      for (int x = 0; x < L.nx; ++x) {
-        const size_t i = row + x;
-        const float4 v = tmp[i];
-        if (rho) rho[i] = fl ? 1.0 + (double)v.w : 0.0;
-        if (u) {
-          u[i] = fl ? v.x : 0.0;
-          u[N + i] = fl ? v.y : 0.0;
-          u[2 * N + i] = fl ? v.z : 0.0;
-        }
-      }
-    }
+  if (!rho && !u) return IBM_LBM_OK;
+  // expanded to the FP64 layout on the device, then one copy per array
+  std::vector<Alloc> tmp;
+  double* d_rho = rho ? (double*)dalloc(h, tmp, sizeof(double) * N) : nullptr;
+  double* d_u = u ? (double*)dalloc(h, tmp, sizeof(double) * 3 * N) : nullptr;
+  if ((rho && !d_rho) || (u && !d_u)) {
+    release_pool(h, tmp);
+    return fail(h, IBM_LBM_E_NOMEM, "get_fields: device allocation failed");
+  }
+  launch_get_moments(L, d_rho, d_u, h->stream);
+  // while the kernel runs: take the page faults of freshly allocated output
+  // arrays on several threads (the copy would take them one by one)
+  touch_pages(rho, sizeof(double) * N);
+  touch_pages(u, sizeof(double) * 3 * N);
+  int rc = IBM_LBM_OK;
+  if (rho && cudaMemcpyAsync(rho, d_rho, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (!rc && u && cudaMemcpyAsync(u, d_u, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IBM_LBM_E_CUDA;
+  release_pool(h, tmp);
+  if (rc) return fail(h, rc, "get_fields: CUDA error");
   return IBM_LBM_OK;
 }
 

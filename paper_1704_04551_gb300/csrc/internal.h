@@ -12,6 +12,8 @@ void launch_collide(const LatticeDev& L, const RowInfo* rows, int n_rows, int st
 void launch_init_equilibrium(const LatticeDev& L, int storage, cudaStream_t st);
 void launch_export(const LatticeDev& L, int storage, bool odd_next, double* out, cudaStream_t st);
 void launch_import(const LatticeDev& L, int storage, const double* in, cudaStream_t st);
+void launch_set_moments(const LatticeDev& L, const double* rho, const double* u, cudaStream_t st);
+void launch_get_moments(const LatticeDev& L, double* rho, double* u, cudaStream_t st);
 void launch_diagnostics(const LatticeDev& L, const RowInfo* rows, int n_rows, double* out, unsigned* umax2_bits,
                         cudaStream_t st);
 

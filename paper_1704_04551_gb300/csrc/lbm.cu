@@ -112,6 +112,33 @@ __global__ void k_import(LatticeDev L, const double* in) {
   for (int i = 0; i < Q; ++i) P::st(A + i * N + idx, i, (float)(in[i * N + idx] - wgt_d(i)));
 }
 
+// Moments between the API's FP64 layout (rho [N], u [3][N]) and the
+// lattice's (u, rho - 1) float4 array: set_lattice's input before the
+// equilibrium initialisation, get_fields' output (solid cells report 0).
+__global__ void k_set_moments(LatticeDev L, const double* rho, const double* u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.N) return;
+  const size_t N = (size_t)L.N;
+  const double r = rho ? rho[i] : 1.0;
+  L.uw[i] = make_float4(u ? (float)u[i] : 0.f, u ? (float)u[N + i] : 0.f, u ? (float)u[2 * N + i] : 0.f,
+                        (float)(r - 1.0));
+}
+
+__global__ void k_get_moments(LatticeDev L, double* rho, double* u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.N) return;
+  const size_t N = (size_t)L.N;
+  const int t = i / L.nx;
+  const bool fl = !solid_yz(L, t % L.ny, t / L.ny);
+  const float4 v = L.uw[i];
+  if (rho) rho[i] = fl ? 1.0 + (double)v.w : 0.0;
+  if (u) {
+    u[i] = fl ? (double)v.x : 0.0;
+    u[N + i] = fl ? (double)v.y : 0.0;
+    u[2 * N + i] = fl ? (double)v.z : 0.0;
+  }
+}
+
 // FP64 sums of the last collision's moments over fluid cells, max |u|, and
 // the finiteness check. out: [0] sum(rho - 1), [1..3] sum rho u, [4] number
 // of fluid cells; *umax2_bits: max |u|^2 as float bits (atomicMax on the
@@ -268,6 +295,14 @@ void launch_import(const LatticeDev& L, int storage, const double* in, cudaStrea
     case STORE_F16: k_import<STORE_F16><<<blocks_for(L.N), 256, 0, st>>>(L, in); break;
     default: k_import<STORE_BF16><<<blocks_for(L.N), 256, 0, st>>>(L, in); break;
   }
+}
+
+void launch_set_moments(const LatticeDev& L, const double* rho, const double* u, cudaStream_t st) {
+  k_set_moments<<<blocks_for(L.N), 256, 0, st>>>(L, rho, u);
+}
+
+void launch_get_moments(const LatticeDev& L, double* rho, double* u, cudaStream_t st) {
+  k_get_moments<<<blocks_for(L.N), 256, 0, st>>>(L, rho, u);
 }
 
 void launch_diagnostics(const LatticeDev& L, const RowInfo* rows, int n_rows, double* out, unsigned* umax2_bits,
