@@ -401,9 +401,12 @@ int prepare_morse(ibm_lbm_t* h) {
   h->morse_ready = false;
   const int M = h->m.M;
   const double rc = h->morse_rc;
+  // neighbour lists: cutoff rc + skin, rebuilt after a move of skin / 2
+  const double skin = 0.3 * rc;
+  constexpr int kListCap = 48;
   const int n[3] = {h->cfg.nx, h->cfg.ny, h->cfg.nz};
   int nb[3];
-  for (int a = 0; a < 3; ++a) nb[a] = std::max(1, (int)std::floor(n[a] / rc));
+  for (int a = 0; a < 3; ++a) nb[a] = std::max(1, (int)std::floor(n[a] / (rc + skin)));
   while ((long long)nb[0] * nb[1] * nb[2] > morse_max_bins()) {
     const int a = nb[0] >= nb[1] && nb[0] >= nb[2] ? 0 : (nb[1] >= nb[2] ? 1 : 2);
     nb[a] = std::max(1, nb[a] / 2);
@@ -414,6 +417,9 @@ int prepare_morse(ibm_lbm_t* h) {
   P.alpha = (float)h->morse_alpha;
   P.r0 = (float)h->morse_r0;
   P.rc2 = (float)(rc * rc);
+  P.rl2 = (float)((rc + skin) * (rc + skin));
+  P.half_skin2 = (float)(0.25 * skin * skin);
+  P.cap = kListCap;
   for (int a = 0; a < 3; ++a) {
     P.nb[a] = nb[a];
     P.inv_bs[a] = (float)nb[a] / (float)n[a];
@@ -429,8 +435,18 @@ int prepare_morse(ibm_lbm_t* h) {
   P.sorted = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
   P.sorted_id = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
   P.bin_owner = (int*)dalloc(h, h->morse_mem, sizeof(int) * P.n_bins);
-  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id || !P.bin_owner)
+  P.ref = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
+  P.cur = (float4*)dalloc(h, h->morse_mem, sizeof(float4) * Mx);
+  P.n_nbr = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx);
+  P.nbr = (int*)dalloc(h, h->morse_mem, sizeof(int) * Mx * kListCap);
+  P.flags = (int*)dalloc(h, h->morse_mem, sizeof(int) * 2);
+  if (!P.count || !P.start || !P.block_sum || !P.bin_of || !P.rank || !P.sorted || !P.sorted_id || !P.bin_owner ||
+      !P.ref || !P.cur || !P.n_nbr || !P.nbr || !P.flags)
     return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
+  const int flags0[2] = {1, 0};  // build the lists at the first step
+  CUDA_TRY(h, cudaMemcpy(P.flags, flags0, sizeof(flags0), cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemset(P.ref, 0, sizeof(float4) * Mx));
+  CUDA_TRY(h, cudaMemset(P.n_nbr, 0, sizeof(int) * Mx));
   CUDA_TRY(h, cudaMemset(P.count, 0, sizeof(int) * P.n_bins));
   CUDA_TRY(h, cudaMemset(P.bin_owner, 0xff, sizeof(int) * P.n_bins));
   CUDA_TRY(h, cudaMemset(P.start, 0, sizeof(int) * ((size_t)P.n_bins + 1)));

@@ -91,6 +91,59 @@ def test_morse_forces_match_oracle(cuda_lib, case):
     assert np.abs(Fg.sum(axis=1)).max() < 1e-4 * scale  # equal and opposite pairs
 
 
+def _sliding_chains(lat, morse, seed):
+    """Dense bead chains (no forces of their own) pushed in different
+    directions, so that neighbours change while they move."""
+    X, bodies = _chains(lat, 60, 8, 0.7, seed=seed, noise=0.1, moduli={})
+    rng = np.random.default_rng(seed + 1)
+    push = np.concatenate([np.repeat(rng.standard_normal((3, 1)), 8, axis=1) for _ in bodies], axis=1)
+    return dict(lattice=lat, mesh=None, bodies=bodies, X=X, morse=morse), 4e-3 * push
+
+
+def test_morse_lists_follow_moving_markers(cuda_lib):
+    """Solid-only steps of sliding chains (terminal speed ~0.02 lu per step,
+    so the lists are rebuilt many times): the trajectory with Morse forces
+    matches the oracle's, which sums every pair directly."""
+    from paper_1704_04551_gb300.binding import Simulation
+    lat, morse = MORSE_CASES['periodic']
+    w, push = _sliding_chains(lat, dict(morse, D0=5e-4), seed=23)
+    sim = Simulation.from_workload(w)
+    ora = O.Oracle.from_workload(w)
+    v = None
+    for _ in range(4):
+        sim.solid_steps(15, 1.0, 0.2, 1.0, push)
+        v = ora.solid_steps(15, 1.0, 0.2, 1.0, push, v=v)
+    Xg, _, Fg = sim.markers()
+    Xo, _, Fo = ora.markers()
+    assert np.abs(Xo - w['X']).max() > 1.0  # moved by several list skins (0.2 lu)
+    assert np.abs(Xg - Xo).max() < 1e-4
+    assert np.abs(Fo).max() > 1e-5, 'no pair within the cutoff'
+    assert np.abs(Fg - Fo).max() < 1e-3 * np.abs(Fo).max()
+
+
+def test_morse_list_overflow_uses_the_full_gather(cuda_lib):
+    """A cutoff wide enough that markers have more neighbours within
+    rc + skin than a list holds: the forces still match the oracle, at the
+    first stage and after the markers have moved."""
+    from paper_1704_04551_gb300.binding import Simulation
+    lat, _ = MORSE_CASES['periodic']
+    w, push = _sliding_chains(lat, dict(D0=1e-6, alpha=0.6, r0=5.0, rc=5.0), seed=29)
+    sim = Simulation.from_workload(w)
+    ora = O.Oracle.from_workload(w)
+    d = np.linalg.norm(w['X'][:, :, None] - w['X'][:, None, :], axis=0)  # no image needed for a lower bound
+    assert (d < 6.5).sum(axis=1).max() > 60  # well above the 48 entries of a list
+    sim.stage(cuda_lib.STAGE_FORCES)
+    ora.stage_forces()
+    Fg, Fo = sim.markers()[2], ora.markers()[2]
+    assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+    sim.solid_steps(10, 1.0, 0.2, 1.0, push)
+    ora.solid_steps(10, 1.0, 0.2, 1.0, push)
+    Xg, _, Fg = sim.markers()
+    Xo, _, Fo = ora.markers()
+    assert np.abs(Xg - Xo).max() < 1e-4
+    assert np.abs(Fg - Fo).max() < 1e-3 * np.abs(Fo).max()
+
+
 def test_coupled_cells_and_filaments_match_oracle(cuda_lib):
     """Three red cells and six 12-bead filaments in a 48 x 40 x 40 channel
     with Morse excluded volume (lattice parameters of the mixed suspension),
