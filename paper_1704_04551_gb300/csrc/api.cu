@@ -51,11 +51,12 @@ void* dalloc(ibm_lbm_t* h, std::vector<Alloc>& pool, size_t bytes) {
   return p;
 }
 
-// Write one byte per page of a host output buffer from several threads, so
-// that the page faults of a freshly allocated buffer are taken in parallel
-// before a device-to-host copy fills it. The buffer is overwritten anyway.
-void touch_pages(void* p, size_t bytes) {
-  if (!p || bytes < ((size_t)64 << 20)) return;
+// Take the page faults of a large host buffer on several threads: one byte
+// per page is written (an output that is about to be overwritten) or read
+// (an input), so that a freshly allocated buffer is mapped in parallel
+// before a copy, which would fault its pages one by one.
+void touch_pages(const void* p, size_t bytes, bool write) {
+  if (!p || bytes < ((size_t)16 << 20)) return;
   const long pg = sysconf(_SC_PAGESIZE);
   const size_t page = pg > 0 ? (size_t)pg : 4096;
   const unsigned nt = std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
@@ -64,9 +65,16 @@ void touch_pages(void* p, size_t bytes) {
   for (unsigned t = 0; t < nt; ++t) {
     const size_t b = t * chunk, e = std::min(bytes, b + chunk);
     if (b >= e) break;
-    th.emplace_back([p, b, e, page] {
-      volatile char* q = static_cast<volatile char*>(p);
-      for (size_t o = b; o < e; o += page) q[o] = 0;
+    th.emplace_back([p, b, e, page, write] {
+      if (write) {
+        volatile char* q = static_cast<volatile char*>(const_cast<void*>(p));
+        for (size_t o = b; o < e; o += page) q[o] = 0;
+      } else {
+        const volatile char* q = static_cast<const volatile char*>(p);
+        char sink = 0;
+        for (size_t o = b; o < e; o += page) sink ^= q[o];
+        (void)sink;
+      }
     });
   }
   for (auto& x : th) x.join();
@@ -576,6 +584,8 @@ int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
     release_pool(h, tmp);
     return fail(h, IBM_LBM_E_NOMEM, "set_lattice: device allocation failed");
   }
+  touch_pages(rho, sizeof(double) * N, false);
+  touch_pages(u, sizeof(double) * 3 * N, false);
   int rc = IBM_LBM_OK;
   if (rho && cudaMemcpyAsync(d_rho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     rc = IBM_LBM_E_CUDA;
@@ -988,8 +998,8 @@ int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
   launch_get_moments(L, d_rho, d_u, h->stream);
   // while the kernel runs: take the page faults of freshly allocated output
   // arrays on several threads (the copy would take them one by one)
-  touch_pages(rho, sizeof(double) * N);
-  touch_pages(u, sizeof(double) * 3 * N);
+  touch_pages(rho, sizeof(double) * N, true);
+  touch_pages(u, sizeof(double) * 3 * N, true);
   int rc = IBM_LBM_OK;
   if (rho && cudaMemcpyAsync(rho, d_rho, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     rc = IBM_LBM_E_CUDA;
@@ -1006,21 +1016,29 @@ int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
   const size_t M = (size_t)h->m.M;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   if (M == 0) return IBM_LBM_OK;
-  if (X) CUDA_TRY(h, cudaMemcpy(X, h->m.X, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost));
-  std::vector<float4> tmp;
-  if (U || F) tmp.resize(M);
-  if (U) {
-    CUDA_TRY(h, cudaMemcpy(tmp.data(), h->m.U, sizeof(float4) * M, cudaMemcpyDeviceToHost));
-    for (size_t k = 0; k < M; ++k) {
-      U[k] = tmp[k].x; U[M + k] = tmp[k].y; U[2 * M + k] = tmp[k].z;
-    }
+  // U and F expanded to the FP64 [3][M] layout on the device
+  std::vector<Alloc> tmp;
+  double* dU = U ? (double*)dalloc(h, tmp, sizeof(double) * 3 * M) : nullptr;
+  double* dF = F ? (double*)dalloc(h, tmp, sizeof(double) * 3 * M) : nullptr;
+  if ((U && !dU) || (F && !dF)) {
+    release_pool(h, tmp);
+    return fail(h, IBM_LBM_E_NOMEM, "get_markers: device allocation failed");
   }
-  if (F) {
-    CUDA_TRY(h, cudaMemcpy(tmp.data(), h->m.F, sizeof(float4) * M, cudaMemcpyDeviceToHost));
-    for (size_t k = 0; k < M; ++k) {
-      F[k] = tmp[k].x; F[M + k] = tmp[k].y; F[2 * M + k] = tmp[k].z;
-    }
-  }
+  if (U) launch_expand_xyz(h->m.U, dU, (int)M, h->stream);
+  if (F) launch_expand_xyz(h->m.F, dF, (int)M, h->stream);
+  touch_pages(X, sizeof(double) * 3 * M, true);
+  touch_pages(U, sizeof(double) * 3 * M, true);
+  touch_pages(F, sizeof(double) * 3 * M, true);
+  int rc = IBM_LBM_OK;
+  if (X && cudaMemcpyAsync(X, h->m.X, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (!rc && U && cudaMemcpyAsync(U, dU, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (!rc && F && cudaMemcpyAsync(F, dF, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = IBM_LBM_E_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IBM_LBM_E_CUDA;
+  release_pool(h, tmp);
+  if (rc) return fail(h, rc, "get_markers: CUDA error");
   return IBM_LBM_OK;
 }
 

@@ -8,6 +8,7 @@
 
 #include "../../include/ibm_lbm.h"
 #include "common.cuh"
+#include "morse.cuh"
 
 namespace ibm {
 constexpr int CHUNK = 16;          // steps per captured chunk graph (even)

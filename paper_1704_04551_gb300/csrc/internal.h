@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "morse.cuh"
 
 namespace ibm {
 
@@ -24,6 +25,7 @@ void launch_interpolate(const LatticeDev& L, const MarkersDev& m, const MarkerGr
                         const int4* boxes, cudaStream_t st);
 cudaError_t transfer_configure();
 void launch_stencil_cache(const MarkersDev& m, cudaStream_t st);
+void launch_expand_xyz(const float4* in, double* out, int M, cudaStream_t st);
 
 // forces.cu
 void launch_forces(const MarkersDev& m, BodyDev* bodies, const int* membranes, int n_membranes, const int* rigids,

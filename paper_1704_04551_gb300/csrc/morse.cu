@@ -25,7 +25,7 @@
 // the lists fit again. Positions come from the stencil cache (floor + FP32
 // fraction), wrapped into the box on periodic axes, so separations are exact
 // to FP32 rounding of a coordinate below the box size.
-#include "common.cuh"
+#include "morse.cuh"
 #include "internal.h"
 
 namespace ibm {

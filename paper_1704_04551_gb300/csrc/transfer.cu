@@ -40,6 +40,21 @@ cudaError_t transfer_configure() {
   return e;
 }
 
+// (x, y, z, -) float4 [M] -> FP64 [3][M] (marker velocities and forces for
+// the API).
+__global__ void k_expand_xyz(const float4* in, double* out, int M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const float4 v = in[k];
+  out[k] = v.x;
+  out[(size_t)M + k] = v.y;
+  out[2 * (size_t)M + k] = v.z;
+}
+
+void launch_expand_xyz(const float4* in, double* out, int M, cudaStream_t st) {
+  if (M > 0) k_expand_xyz<<<(M + 255) / 256, 256, 0, st>>>(in, out, M);
+}
+
 void launch_stencil_cache(const MarkersDev& m, cudaStream_t st) {
   if (m.M == 0) return;
   k_stencil_cache<<<(m.M + 255) / 256, 256, 0, st>>>(m);
