@@ -61,22 +61,30 @@ void touch_pages(const void* p, size_t bytes, bool write) {
   const size_t page = pg > 0 ? (size_t)pg : 4096;
   const unsigned nt = std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
   const size_t chunk = (bytes / nt + page - 1) / page * page;
+  auto touch = [p, page, write](size_t b, size_t e) {
+    if (write) {
+      volatile char* q = static_cast<volatile char*>(const_cast<void*>(p));
+      for (size_t o = b; o < e; o += page) q[o] = 0;
+    } else {
+      const volatile char* q = static_cast<const volatile char*>(p);
+      char sink = 0;
+      for (size_t o = b; o < e; o += page) sink ^= q[o];
+      (void)sink;
+    }
+  };
   std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t) {
-    const size_t b = t * chunk, e = std::min(bytes, b + chunk);
-    if (b >= e) break;
-    th.emplace_back([p, b, e, page, write] {
-      if (write) {
-        volatile char* q = static_cast<volatile char*>(const_cast<void*>(p));
-        for (size_t o = b; o < e; o += page) q[o] = 0;
-      } else {
-        const volatile char* q = static_cast<const volatile char*>(p);
-        char sink = 0;
-        for (size_t o = b; o < e; o += page) sink ^= q[o];
-        (void)sink;
-      }
-    });
+  size_t done = 0;  // [0, done) is handed to threads
+  try {
+    for (unsigned t = 0; t < nt; ++t) {
+      const size_t b = t * chunk, e = std::min(bytes, b + chunk);
+      if (b >= e) break;
+      th.emplace_back(touch, b, e);
+      done = e;
+    }
+  } catch (...) {
+    // no more threads: the calling thread takes the rest (an optimisation only)
   }
+  touch(done, bytes);
   for (auto& x : th) x.join();
 }
 
