@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -25,6 +26,31 @@ namespace {
 
 int fail(ibm_lbm_t* h, int code, const std::string& msg) {
   if (h) h->err = msg;
+  return code;
+}
+
+// No C++ exception crosses the C ABI: every entry point runs its body under
+// this guard; a failed host allocation returns E_NOMEM, any other exception
+// (e.g. a size the standard containers reject) E_ARG.
+template <class F>
+int abi_guard(ibm_lbm_t* h, F&& body) noexcept {
+  const char* msg = nullptr;
+  int code = IBM_LBM_OK;
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    code = IBM_LBM_E_NOMEM;
+    msg = "host allocation failed";
+  } catch (...) {
+    code = IBM_LBM_E_ARG;
+    msg = "invalid size or argument (host exception)";
+  }
+  if (h) {
+    try {
+      h->err = msg;
+    } catch (...) {
+    }
+  }
   return code;
 }
 
@@ -485,7 +511,7 @@ void* ibm_lbm_stream(ibm_lbm_t* h) { return h ? (void*)h->stream : nullptr; }
 
 size_t ibm_lbm_device_bytes(const ibm_lbm_t* h) { return h ? h->bytes : 0; }
 
-int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, void* stream, ibm_lbm_t** out) {
+static int impl_ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, void* stream, ibm_lbm_t** out) {
   if (!cfg || !out) return IBM_LBM_E_ARG;
   *out = nullptr;
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
@@ -563,7 +589,7 @@ int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, vo
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_destroy(ibm_lbm_t* h) {
+static int impl_ibm_lbm_destroy(ibm_lbm_t* h) {
   if (!h) return IBM_LBM_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto e : h->events) cudaEventDestroy(e);
@@ -578,7 +604,7 @@ int ibm_lbm_destroy(ibm_lbm_t* h) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
+static int impl_ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
   if (!h) return IBM_LBM_E_ARG;
   LatticeDev& L = h->L;
   const size_t N = (size_t)L.N;
@@ -616,7 +642,7 @@ int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
+static int impl_ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
   if (!h || !f) return fail(h, IBM_LBM_E_ARG, "null argument");
   std::vector<Alloc> tmp;
   const size_t bytes = sizeof(double) * Q * (size_t)h->L.N;
@@ -638,7 +664,7 @@ int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
+static int impl_ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
   if (!h || !f) return fail(h, IBM_LBM_E_ARG, "null argument");
   std::vector<Alloc> tmp;
   const size_t bytes = sizeof(double) * Q * (size_t)h->L.N;
@@ -654,7 +680,7 @@ int ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
+static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
                         int64_t n_markers, const double* X) {
   if (!h) return IBM_LBM_E_ARG;
   if (n_bodies < 0 || n_markers < 0 || n_markers >= (1LL << 31) || (n_markers > 0 && !X) ||
@@ -871,7 +897,7 @@ int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext) {
+static int impl_ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext) {
   if (!h) return IBM_LBM_E_ARG;
   if (n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0) || !(mass > 0.0))
     return fail(h, IBM_LBM_E_ARG, "solid_steps: needs n_steps >= 0, dt > 0, gamma >= 0, mass > 0");
@@ -905,7 +931,7 @@ int ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, 
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double rc) {
+static int impl_ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double rc) {
   if (!h) return IBM_LBM_E_ARG;
   if (rc > 0.0 && (!(D0 >= 0.0) || !(alpha > 0.0) || !std::isfinite(r0) || !std::isfinite(rc)))
     return fail(h, IBM_LBM_E_ARG, "set_morse: needs D0 >= 0, alpha > 0 and finite r0, rc");
@@ -921,24 +947,24 @@ int ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double r
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_step_async(ibm_lbm_t* h, int64_t n_steps) {
+static int impl_ibm_lbm_step_async(ibm_lbm_t* h, int64_t n_steps) {
   if (!h) return IBM_LBM_E_ARG;
   return enqueue_steps(h, n_steps);
 }
 
-int ibm_lbm_synchronize(ibm_lbm_t* h) {
+static int impl_ibm_lbm_synchronize(ibm_lbm_t* h) {
   if (!h) return IBM_LBM_E_ARG;
   return finish_diagnostics(h);
 }
 
-int ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps) {
+static int impl_ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps) {
   if (!h) return IBM_LBM_E_ARG;
   int rc = enqueue_steps(h, n_steps);
   if (rc) return rc;
   return finish_diagnostics(h);
 }
 
-int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
+static int impl_ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
   if (!h) return IBM_LBM_E_ARG;
   cudaStream_t st = h->stream;
   switch (stage) {
@@ -967,7 +993,7 @@ int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F) {
+static int impl_ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F) {
   if (!h || (!F && h->m.M > 0)) return fail(h, IBM_LBM_E_ARG, "null argument");
   const size_t M = (size_t)h->m.M;
   std::vector<float4> tmp(M);
@@ -977,7 +1003,7 @@ int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
+static int impl_ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
   if (!h || !g) return fail(h, IBM_LBM_E_ARG, "null argument");
   const size_t N = (size_t)h->L.N;
   std::vector<float4> tmp(N);
@@ -989,7 +1015,7 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
+static int impl_ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
   if (!h) return IBM_LBM_E_ARG;
   const LatticeDev& L = h->L;
   const size_t N = (size_t)L.N;
@@ -1019,7 +1045,7 @@ int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
+static int impl_ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
   if (!h) return IBM_LBM_E_ARG;
   const size_t M = (size_t)h->m.M;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1050,7 +1076,7 @@ int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
+static int impl_ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
   if (!h || n_bodies != h->n_bodies || (n_bodies > 0 && !bodies))
     return fail(h, IBM_LBM_E_ARG, "get_bodies: count mismatch");
   if (n_bodies == 0) return IBM_LBM_OK;
@@ -1068,7 +1094,7 @@ int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
+static int impl_ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   if (!h || max_steps < 0 || max_steps > (1 << 22)) return fail(h, IBM_LBM_E_ARG, "set_timing: bad step count");
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   for (auto e : h->events) cudaEventDestroy(e);
@@ -1084,7 +1110,7 @@ int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
+static int impl_ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
   if (!h || !out) return IBM_LBM_E_ARG;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
@@ -1101,7 +1127,7 @@ int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]) {
+static int impl_ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]) {
   if (!h || !out) return IBM_LBM_E_ARG;
   int rc = enqueue_diagnostics(h);
   if (rc) return rc;
@@ -1120,4 +1146,85 @@ int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]) {
   return IBM_LBM_OK;
 }
 
+
+int ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocator* alloc, void* stream, ibm_lbm_t** out) {
+  return abi_guard(nullptr, [&]() -> int { return impl_ibm_lbm_create(cfg, alloc, stream, out); });
+}
+
+int ibm_lbm_destroy(ibm_lbm_t* h) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_destroy(h); });
+}
+
+int ibm_lbm_set_lattice(ibm_lbm_t* h, const double* rho, const double* u) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_lattice(h, rho, u); });
+}
+
+int ibm_lbm_set_populations(ibm_lbm_t* h, const double* f) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_populations(h, f); });
+}
+
+int ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_populations(h, f); });
+}
+
+int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
+                        int64_t n_markers, const double* X) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_markers(h, mesh, n_bodies, bodies, n_markers, X); });
+}
+
+int ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_solid_steps(h, n_steps, dt, gamma, mass, f_ext); });
+}
+
+int ibm_lbm_set_morse(ibm_lbm_t* h, double D0, double alpha, double r0, double rc) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_morse(h, D0, alpha, r0, rc); });
+}
+
+int ibm_lbm_step_async(ibm_lbm_t* h, int64_t n_steps) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_step_async(h, n_steps); });
+}
+
+int ibm_lbm_synchronize(ibm_lbm_t* h) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_synchronize(h); });
+}
+
+int ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_step(h, n_steps); });
+}
+
+int ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_run_stage(h, stage); });
+}
+
+int ibm_lbm_set_marker_forces(ibm_lbm_t* h, const double* F) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_marker_forces(h, F); });
+}
+
+int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_force_density(h, g); });
+}
+
+int ibm_lbm_get_fields(ibm_lbm_t* h, double* rho, double* u) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_fields(h, rho, u); });
+}
+
+int ibm_lbm_get_markers(ibm_lbm_t* h, double* X, double* U, double* F) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_markers(h, X, U, F); });
+}
+
+int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_bodies(h, bodies, n_bodies); });
+}
+
+int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_timing(h, max_steps); });
+}
+
+int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_timing(h, out); });
+}
+
+int ibm_lbm_get_diagnostics(ibm_lbm_t* h, double out[8]) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_get_diagnostics(h, out); });
+}
 }  // extern "C"

@@ -26,6 +26,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -214,6 +215,30 @@ namespace {
 
 int sfail(ibm_lbm_server_t* s, int code, const std::string& msg) {
   if (s) s->err = msg;
+  return code;
+}
+
+// No C++ exception crosses the C ABI (as for the handle calls): a failed
+// host allocation returns E_NOMEM, any other exception E_ARG.
+template <class F>
+int server_guard(ibm_lbm_server_t* s, F&& body) noexcept {
+  const char* msg = nullptr;
+  int code = IBM_LBM_OK;
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    code = IBM_LBM_E_NOMEM;
+    msg = "host allocation failed";
+  } catch (...) {
+    code = IBM_LBM_E_ARG;
+    msg = "invalid size or argument (host exception)";
+  }
+  if (s) {
+    try {
+      s->err = msg;
+    } catch (...) {
+    }
+  }
   return code;
 }
 
@@ -456,7 +481,7 @@ int retire(ibm_lbm_server_t* s, ibm_lbm_server::Case* c) {
 
 extern "C" {
 
-int ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
+static int impl_ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
                           ibm_lbm_server_t** out) {
   if (!cfg || !out || cfg->max_active < 1 || cfg->chunk_steps < 2 || (cfg->chunk_steps & 1) ||
       cfg->device_mem_budget == 0 || (alloc && (!alloc->alloc || !alloc->release)))
@@ -499,7 +524,7 @@ int ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_alloca
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_server_destroy(ibm_lbm_server_t* s) {
+static int impl_ibm_lbm_server_destroy(ibm_lbm_server_t* s) {
   if (!s) return IBM_LBM_OK;
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -513,7 +538,7 @@ int ibm_lbm_server_destroy(ibm_lbm_server_t* s) {
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t* id) {
+static int impl_ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t* id) {
   if (!s || !in || !id) return sfail(s, IBM_LBM_E_ARG, "submit: null argument");
   const ibm_lbm_config& L = in->lattice;
   if (L.storage != IBM_LBM_STORE_F32) return sfail(s, IBM_LBM_E_ARG, "submit: served cases use FP32 storage");
@@ -553,7 +578,7 @@ int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t*
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_server_advance(ibm_lbm_server_t* s, int32_t* n_running, int32_t* n_pending, int32_t* n_done) {
+static int impl_ibm_lbm_server_advance(ibm_lbm_server_t* s, int32_t* n_running, int32_t* n_pending, int32_t* n_done) {
   if (!s) return IBM_LBM_E_ARG;
   int rc = admit(s);
   if (rc) return rc;
@@ -589,7 +614,7 @@ int ibm_lbm_server_advance(ibm_lbm_server_t* s, int32_t* n_running, int32_t* n_p
   return status;
 }
 
-int ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* state, int64_t* steps_done) {
+static int impl_ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* state, int64_t* steps_done) {
   if (!s) return IBM_LBM_E_ARG;
   auto it = s->cases.find(id);
   if (it == s->cases.end()) return sfail(s, IBM_LBM_E_ARG, "poll: unknown case");
@@ -598,7 +623,7 @@ int ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* state, int64_
   return IBM_LBM_OK;
 }
 
-int ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double* u, double* X, double* U,
+static int impl_ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double* u, double* X, double* U,
                           ibm_lbm_body* bodies, int32_t n_bodies) {
   if (!s) return IBM_LBM_E_ARG;
   auto it = s->cases.find(id);
@@ -617,4 +642,30 @@ int ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double*
 
 const char* ibm_lbm_server_last_error(const ibm_lbm_server_t* s) { return s ? s->err.c_str() : "null server"; }
 
+
+int ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
+                          ibm_lbm_server_t** out) {
+  return server_guard(nullptr, [&]() -> int { return impl_ibm_lbm_server_create(cfg, alloc, stream, out); });
+}
+
+int ibm_lbm_server_destroy(ibm_lbm_server_t* s) {
+  return server_guard(s, [&]() -> int { return impl_ibm_lbm_server_destroy(s); });
+}
+
+int ibm_lbm_server_submit(ibm_lbm_server_t* s, const ibm_lbm_case* in, uint64_t* id) {
+  return server_guard(s, [&]() -> int { return impl_ibm_lbm_server_submit(s, in, id); });
+}
+
+int ibm_lbm_server_advance(ibm_lbm_server_t* s, int32_t* n_running, int32_t* n_pending, int32_t* n_done) {
+  return server_guard(s, [&]() -> int { return impl_ibm_lbm_server_advance(s, n_running, n_pending, n_done); });
+}
+
+int ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* state, int64_t* steps_done) {
+  return server_guard(s, [&]() -> int { return impl_ibm_lbm_server_poll(s, id, state, steps_done); });
+}
+
+int ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double* u, double* X, double* U,
+                          ibm_lbm_body* bodies, int32_t n_bodies) {
+  return server_guard(s, [&]() -> int { return impl_ibm_lbm_server_result(s, id, rho, u, X, U, bodies, n_bodies); });
+}
 }  // extern "C"
