@@ -46,3 +46,19 @@ def test_binding_signatures_load(libpath):
     cfg.tau = 0.4
     assert L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == binding.E_ARG
     assert L.ibm_lbm_destroy(None) == 0
+
+
+def test_calls_without_a_device_fail_with_a_status(libpath):
+    """With no CUDA device, a valid configuration is refused with an error
+    code (no abort, no handle), and so is a server."""
+    torch = pytest.importorskip('torch')
+    if torch.cuda.is_available():
+        pytest.skip('a CUDA device is present')
+    L = binding.load()
+    cfg = binding.Config()
+    cfg.nx = cfg.ny = cfg.nz = 16
+    cfg.tau = 0.8
+    out = ctypes.c_void_p()
+    rc = L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out))
+    assert rc in (binding.E_CUDA, binding.E_NOMEM)
+    assert not out.value
