@@ -681,7 +681,7 @@ static int impl_ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
 }
 
 static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
-                        int64_t n_markers, const double* X) {
+                                    int64_t n_markers, const double* X) {
   if (!h) return IBM_LBM_E_ARG;
   if (n_bodies < 0 || n_markers < 0 || n_markers >= (1LL << 31) || (n_markers > 0 && !X) ||
       (n_bodies > 0 && !bodies))

@@ -482,7 +482,7 @@ int retire(ibm_lbm_server_t* s, ibm_lbm_server::Case* c) {
 extern "C" {
 
 static int impl_ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ibm_lbm_allocator* alloc, void* stream,
-                          ibm_lbm_server_t** out) {
+                                      ibm_lbm_server_t** out) {
   if (!cfg || !out || cfg->max_active < 1 || cfg->chunk_steps < 2 || (cfg->chunk_steps & 1) ||
       cfg->device_mem_budget == 0 || (alloc && (!alloc->alloc || !alloc->release)))
     return IBM_LBM_E_ARG;
@@ -624,7 +624,7 @@ static int impl_ibm_lbm_server_poll(ibm_lbm_server_t* s, uint64_t id, int32_t* s
 }
 
 static int impl_ibm_lbm_server_result(ibm_lbm_server_t* s, uint64_t id, double* rho, double* u, double* X, double* U,
-                          ibm_lbm_body* bodies, int32_t n_bodies) {
+                                      ibm_lbm_body* bodies, int32_t n_bodies) {
   if (!s) return IBM_LBM_E_ARG;
   auto it = s->cases.find(id);
   if (it == s->cases.end()) return sfail(s, IBM_LBM_E_ARG, "result: unknown case");
