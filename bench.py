@@ -306,11 +306,13 @@ def run_reference(args):
     oracle.build()
     w = cpu_sample(args.workload)
     # each requested step is bounded: at most a couple of full oracle steps
-    # are timed so that the whole run ends within a few minutes
+    # are timed, after at most three untimed ones, so that the whole run ends
+    # within a few minutes
     n = max(1, min(args.steps, args.ref_max_steps))
-    r = time_oracle(w, n, warmup=min(args.warmup, 0))
+    wu = max(0, min(args.warmup, 3))
+    r = time_oracle(w, n, warmup=wu)
     line = dict(impl='reference', metric=METRIC, value=r['mlups'], unit=UNIT, n_gpus=args.gpus, steps=n,
-                warmup=0, ms_per_step=1e3 * r['seconds'] / n, higher_is_better=True, scaling='weak',
+                warmup=wu, ms_per_step=1e3 * r['seconds'] / n, higher_is_better=True, scaling='weak',
                 vs_baseline=None, dtype='f64', data='synthetic',
                 config=dict(workload=w['label'], requested_steps=args.steps, lattice=[w['lattice'][k] for k in ('nx', 'ny', 'nz')],
                             markers=int(w['X'].shape[1]), bodies=len(w['bodies'])),
