@@ -183,10 +183,20 @@ def ibm_lbm_get_populations(h, f):
 
 
 def ibm_lbm_set_markers(h, mesh: Mesh | None, bodies, X):
+    """bodies: a list of Body records, or the structured array body_array
+    returns (the same bytes, filled without a Python object per body)."""
     X = _f64(X)
-    arr = (Body * max(1, len(bodies)))(*bodies) if bodies else (Body * 1)()
+    if isinstance(bodies, np.ndarray):
+        assert bodies.dtype == BODY_DTYPE and bodies.flags.c_contiguous
+        n = len(bodies)
+        arr = bodies if n else np.zeros(1, dtype=BODY_DTYPE)
+        ptr = arr.ctypes.data
+    else:
+        n = len(bodies)
+        arr = (Body * max(1, n))(*bodies) if bodies else (Body * 1)()
+        ptr = C.cast(arr, C.c_void_p)
     return _check(h, load().ibm_lbm_set_markers(h, C.byref(mesh) if mesh is not None else None,
-                                                len(bodies), arr, X.shape[1], _p(X)))
+                                                n, ptr, X.shape[1], _p(X)))
 
 
 def ibm_lbm_set_morse(h, D0, alpha, r0, rc):
@@ -370,6 +380,26 @@ def make_config(lattice: dict, storage='f32', device=0) -> Config:
     return cfg
 
 
+_BODY_SCALARS = ('kBT_p', 'k_b', 'k_l', 'k_g', 'k_v', 'kappa', 'mass')
+_BODY_VECTORS = (('inertia', 3), ('center', 3), ('quat', 4), ('vel', 3), ('omega', 3))
+# ibm_lbm_body as a numpy record (naturally aligned, no padding beyond `pad`)
+BODY_DTYPE = np.dtype([('kind', '<i4'), ('pad', '<i4'), ('first', '<i8'), ('count', '<i8')] +
+                      [(k, '<f8') for k in _BODY_SCALARS] + [(k, '<f8', (n,)) for k, n in _BODY_VECTORS] +
+                      [('l0', '<f8')])
+
+
+def body_array(bodies) -> np.ndarray:
+    """Body dicts (as make_body takes them) as one ibm_lbm_body array."""
+    if not bodies:
+        return np.zeros(0, dtype=BODY_DTYPE)
+    z3, q0 = (0.0, 0.0, 0.0), (1.0, 0.0, 0.0, 0.0)
+    rows = [(d['kind'], 0, d['first'], d['count'], d.get('kBT_p', 0.0), d.get('k_b', 0.0), d.get('k_l', 0.0),
+             d.get('k_g', 0.0), d.get('k_v', 0.0), d.get('kappa', 0.0), d.get('mass', 0.0),
+             tuple(d.get('inertia', z3))[:3], tuple(d.get('center', z3))[:3], tuple(d.get('quat', q0))[:4],
+             tuple(d.get('vel', z3))[:3], tuple(d.get('omega', z3))[:3], d.get('l0', 0.0)) for d in bodies]
+    return np.array(rows, dtype=BODY_DTYPE)
+
+
 def make_body(d) -> Body:
     b = Body()
     b.kind, b.first, b.count = int(d['kind']), int(d['first']), int(d['count'])
@@ -453,7 +483,7 @@ class Simulation:
             rest = _f64(mesh['rest_X'])
             self._mesh_arrays = (tris, rest)
             m = Mesh(rest.shape[1], tris.shape[0], tris.ctypes.data, rest.ctypes.data)
-        ibm_lbm_set_markers(self.h, m, [make_body(b) for b in bodies], X)
+        ibm_lbm_set_markers(self.h, m, body_array(bodies), X)
         self.M = X.shape[1]
         self.n_bodies = len(bodies)
 
