@@ -62,3 +62,20 @@ def test_calls_without_a_device_fail_with_a_status(libpath):
     rc = L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out))
     assert rc in (binding.E_CUDA, binding.E_NOMEM)
     assert not out.value
+
+
+def test_body_array_matches_the_ctypes_records():
+    """The numpy body records passed to ibm_lbm_set_markers have the C
+    layout of ibm_lbm_body: same size and offsets, and the same bytes as the
+    per-body ctypes records, for every body kind."""
+    from paper_1704_04551_gb300 import inputs as I
+    assert binding.BODY_DTYPE.itemsize == ctypes.sizeof(binding.Body)
+    for name, _ in binding.Body._fields_:
+        assert binding.BODY_DTYPE.fields[name][1] == getattr(binding.Body, name).offset, name
+    cases = [I.rbc_tube(n=40, radius=18.0, n_cells=2, seed=3, freq=5, steps=0)['bodies'],
+             I.shear_ellipsoid(n=24, seed=3)['bodies'], I.shear_ellipsoid(n=24, seed=3, direct=True)['bodies'],
+             I.mixed_suspension(shape=(48, 40, 40), n_cells=2, n_filaments=3, beads=6, seed=5)['bodies']]
+    for bodies in cases:
+        ref = (binding.Body * len(bodies))(*[binding.make_body(b) for b in bodies])
+        assert binding.body_array(bodies).tobytes() == ctypes.string_at(ctypes.addressof(ref), ctypes.sizeof(ref))
+    assert binding.body_array([]).shape == (0,)
