@@ -76,11 +76,16 @@ def test_spinning_body_in_fluid_at_rest_torque_closed_form():
     f_solid = -kappa * np.cross(omega, r.T).T
     assert np.allclose(F, -f_solid, atol=1e-16)
     T = -kappa * ((r * r).sum(axis=0).sum() * omega - r @ (r.T @ omega))
+    # Euler's equations with torque, per component in the body frame:
+    # I1 dw1 = t1 + (I2 - I3) w2 w3 and cyclic shifts (dt = 1)
     R = I.quat_to_matrix(b['quat'])
-    wb, tb = R.T @ omega, R.T @ T
-    Iv = np.array(b['inertia'])
-    wb_new = wb + (tb - np.cross(wb, Iv * wb)) / Iv
-    assert np.allclose(o.body(0)['omega'], R @ wb_new, rtol=1e-12, atol=1e-18)
+    w, t = R.T @ omega, R.T @ T
+    nb = R.T @ np.array(o.body(0)['omega'])
+    I1, I2, I3 = b['inertia']
+    expect = (t[0] + (I2 - I3) * w[1] * w[2], t[1] + (I3 - I1) * w[2] * w[0], t[2] + (I1 - I2) * w[0] * w[1])
+    got = (I1 * (nb[0] - w[0]), I2 * (nb[1] - w[1]), I3 * (nb[2] - w[2]))
+    for g, e in zip(got, expect):
+        assert abs(g - e) <= 1e-10 * abs(e) + 1e-22
 
 
 def test_momentum_exchange_and_rigidity_over_coupled_steps():
