@@ -66,8 +66,12 @@ enum { IBM_LBM_STAGE_FORCES = 0, IBM_LBM_STAGE_SPREAD = 1, IBM_LBM_STAGE_COLLIDE
        IBM_LBM_STAGE_INTERP = 3 };
 
 /* Device-memory provider. alloc returns a device pointer aligned to at
- * least 256 bytes, or NULL; release frees it. Called only from create,
- * set_markers and destroy, on the calling thread. */
+ * least 256 bytes, or NULL (the call that needed the memory then returns
+ * IBM_LBM_E_NOMEM and releases what it took); release frees it. Called only
+ * from the calls that take or return device memory (create, set_lattice,
+ * set_populations, get_populations, set_markers, set_morse, solid_steps,
+ * destroy, and the server's submit, advance and destroy), on the calling
+ * thread. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*release)(void* ptr, void* ctx);
@@ -165,7 +169,9 @@ int ibm_lbm_get_populations(ibm_lbm_t* h, double* f);
  * lattice units, finite with |X| < 2^30. Markers outside every body are
  * passive tracers (zero force). Errors: E_ARG (overlapping or out-of-range
  * bodies, membrane count != n_vertices, non-manifold mesh, template too
- * large, a non-finite or too large position), E_NOMEM. */
+ * large, a non-finite or too large position), E_NOMEM. The previous markers
+ * are dropped first; after any error the handle holds no markers (a lattice
+ * alone, which can still step) and none of the failed call's memory. */
 int ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies,
                         const ibm_lbm_body* bodies, int64_t n_markers, const double* X);
 
@@ -317,19 +323,26 @@ const char* ibm_lbm_server_last_error(const ibm_lbm_server_t* s);
  * loads this library holds until the process exits.
  *
  * Inputs (device pointers owned by the caller): X [3][M] FP64 marker
- * positions, F [3][M] FP64 marker forces. Output: g [3][N] FP64 force
+ * positions, F [3][M] FP64 marker forces. X is not visible to the host, so
+ * it is checked on the device: a marker whose position is not finite or has
+ * a coordinate with |x| >= 2^30 (the bound ibm_lbm_set_markers enforces)
+ * contributes nothing; non-finite forces give non-finite density. Output: g [3][N] FP64 force
  * density, N = nx*ny*nz, fully overwritten (cells outside every stencil get
  * 0). geometry / tube_radius as in ibm_lbm_config; stream is a cudaStream_t
  * or NULL. The call only enqueues work on the stream and returns; g is ready
  * when the stream reaches that point.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.
+ * Every call looks up the array's device address in the current context
+ * (so a device reset by the caller is safe); the first call on a device may
+ * load the library's device code there, so make it before any stream
+ * capture.
  * Every call shares the one array per device and clears it first, so calls
  * whose work overlaps on the GPU (different streams, host threads) race and
  * must be serialised by the caller.
  * Errors: IBM_LBM_E_ARG if nx*ny*nz > IBM_LBM_NOALLOC_MAX_CELLS, any
- * dimension < 4, M < 0, a null pointer with M > 0 or N > 0, or an unknown
- * geometry; IBM_LBM_E_CUDA if the address lookup or a launch fails. */
+ * dimension < 4, M < 0 or M >= 2^31, X or F null with M > 0, g null, an
+ * unknown geometry, or geometry 2 (tube) with tube_radius <= 0 (also for any
+ * host exception; none crosses this boundary); IBM_LBM_E_CUDA if the
+ * address lookup, the clearing of the array or a launch fails. */
 #define IBM_LBM_NOALLOC_MAX_CELLS (1 << 20)
 int ibm_lbm_spread_noalloc(const double* X, const double* F, int64_t n_markers, int32_t nx, int32_t ny,
                            int32_t nz, int32_t geometry, double tube_radius, double* g, void* stream);

@@ -416,17 +416,20 @@ def make_body(d) -> Body:
 class Simulation:
     """One lattice with its markers on one GPU (wraps an ibm_lbm handle)."""
 
-    def __init__(self, lattice: dict, storage='f32', device=0, use_torch=True, stream=None):
+    def __init__(self, lattice: dict, storage='f32', device=0, use_torch=True, stream=None, memory=None):
+        """memory: an object with an ``Allocator`` in ``.struct`` (default:
+        TorchMemory when use_torch, else cudaMalloc inside the library)."""
         self.shape = (int(lattice['nx']), int(lattice['ny']), int(lattice['nz']))
         self.N = int(np.prod(self.shape))
         self.M = 0
         self.n_bodies = 0
-        self._mem = None
+        self._mem = memory
         self._stream_obj = None
         if use_torch:
             import torch
             dev = torch.device('cuda', device)
-            self._mem = TorchMemory(dev)
+            if self._mem is None:
+                self._mem = TorchMemory(dev)
             if stream is None:
                 self._stream_obj = torch.cuda.Stream(device=dev)
                 stream = self._stream_obj.cuda_stream
@@ -550,13 +553,15 @@ class Server:
     ibm_lbm_server). Cases are workload dicts as for Simulation.from_workload
     plus a step count."""
 
-    def __init__(self, device_mem_budget, max_active=64, chunk_steps=100, device=0, use_torch=True, stream=None):
-        self._mem = None
+    def __init__(self, device_mem_budget, max_active=64, chunk_steps=100, device=0, use_torch=True, stream=None,
+                 memory=None):
+        self._mem = memory
         self._stream_obj = None
         if use_torch:
             import torch
             dev = torch.device('cuda', device)
-            self._mem = TorchMemory(dev)
+            if self._mem is None:
+                self._mem = TorchMemory(dev)
             if stream is None:
                 self._stream_obj = torch.cuda.Stream(device=dev)
                 stream = self._stream_obj.cuda_stream

@@ -237,6 +237,7 @@ int finish_diagnostics(ibm_lbm_t* h) {
 int enqueue_steps(ibm_lbm_t* h, int64_t n) {
   if (n < 0) return fail(h, IBM_LBM_E_ARG, "n_steps < 0");
   if (n == 0) return IBM_LBM_OK;
+  h->boxes_valid = false;  // the last interpolation moves the markers
   int64_t left = n;
   if (h->timing) {
     for (; left > 0; --left) {
@@ -680,13 +681,9 @@ static int impl_ibm_lbm_get_populations(ibm_lbm_t* h, double* f) {
   return IBM_LBM_OK;
 }
 
-static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
-                                    int64_t n_markers, const double* X) {
-  if (!h) return IBM_LBM_E_ARG;
-  if (n_bodies < 0 || n_markers < 0 || n_markers >= (1LL << 31) || (n_markers > 0 && !X) ||
-      (n_bodies > 0 && !bodies))
-    return fail(h, IBM_LBM_E_ARG, "set_markers: bad counts or null arrays");
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+// Forget the markers, bodies, template and Morse lists (and the graphs that
+// captured them): the handle is then a lattice without markers.
+static void clear_markers(ibm_lbm_t* h) {
   drop_graphs(h);
   release_pool(h, h->morse_mem);
   release_pool(h, h->marker_mem);
@@ -705,6 +702,13 @@ static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int3
   h->groups = nullptr;
   h->n_groups = 0;
   h->boxes = nullptr;
+  h->need_zero_F = false;
+}
+
+// set_markers after the old markers are gone; on error the caller clears
+// whatever this allocated, so that a failed call leaves no half-built state.
+static int set_markers_into(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
+                     int64_t n_markers, const double* X) {
   const int M = (int)n_markers;
   // validate bodies
   std::vector<std::pair<int64_t, int64_t>> ranges;
@@ -897,6 +901,23 @@ static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int3
   return IBM_LBM_OK;
 }
 
+static int impl_ibm_lbm_set_markers(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bodies, const ibm_lbm_body* bodies,
+                                    int64_t n_markers, const double* X) {
+  if (!h) return IBM_LBM_E_ARG;
+  if (n_bodies < 0 || n_markers < 0 || n_markers >= (1LL << 31) || (n_markers > 0 && !X) ||
+      (n_bodies > 0 && !bodies))
+    return fail(h, IBM_LBM_E_ARG, "set_markers: bad counts or null arrays");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  clear_markers(h);
+  const int rc = set_markers_into(h, mesh, n_bodies, bodies, n_markers, X);
+  if (rc != IBM_LBM_OK) {
+    const std::string why = h->err;
+    clear_markers(h);
+    h->err = why;
+  }
+  return rc;
+}
+
 static int impl_ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, double gamma, double mass, const double* f_ext) {
   if (!h) return IBM_LBM_E_ARG;
   if (n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0) || !(mass > 0.0))
@@ -916,7 +937,10 @@ static int impl_ibm_lbm_solid_steps(ibm_lbm_t* h, int64_t n_steps, double dt, do
   if (f_ext) {
     fe = (double*)dalloc(h, tmp, sizeof(double) * 3 * M);
     if (!fe) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
-    CUDA_TRY(h, cudaMemcpy(fe, f_ext, sizeof(double) * 3 * M, cudaMemcpyHostToDevice));
+    if (cudaMemcpy(fe, f_ext, sizeof(double) * 3 * M, cudaMemcpyHostToDevice) != cudaSuccess) {
+      release_pool(h, tmp);
+      return fail(h, IBM_LBM_E_CUDA, "solid_steps: copy of f_ext failed");
+    }
   }
   for (int64_t s = 0; s < n_steps; ++s) {
     enqueue_forces(h, st);
@@ -967,14 +991,21 @@ static int impl_ibm_lbm_step(ibm_lbm_t* h, int64_t n_steps) {
 static int impl_ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
   if (!h) return IBM_LBM_E_ARG;
   cudaStream_t st = h->stream;
+  // The interpolation gathers from the stencil boxes the last spreading
+  // computed; they hold the markers only while no stage has moved them since
+  // (the interpolation advects, the direct rigid forcing places markers).
+  // Otherwise the boxes are cleared first and every marker takes the
+  // per-marker path.
   switch (stage) {
     case IBM_LBM_STAGE_FORCES:
       enqueue_forces(h, st);
+      h->boxes_valid = false;
       break;
     case IBM_LBM_STAGE_SPREAD: {
       const LatticeDev L = lat(h, h->odd_next);
       CUDA_TRY(h, cudaMemsetAsync(L.flags, 0, (size_t)tiles(L), st));
       launch_spread(L, h->m, h->groups, h->n_groups, h->boxes, st);
+      h->boxes_valid = true;
       break;
     }
     case IBM_LBM_STAGE_COLLIDE:
@@ -982,7 +1013,10 @@ static int impl_ibm_lbm_run_stage(ibm_lbm_t* h, int32_t stage) {
       h->odd_next = !h->odd_next;
       break;
     case IBM_LBM_STAGE_INTERP:
+      if (!h->boxes_valid && h->n_groups > 0)
+        CUDA_TRY(h, cudaMemsetAsync(h->boxes, 0, sizeof(int4) * 2 * (size_t)h->n_groups, st));
       launch_interpolate(h->L, h->m, h->groups, h->n_groups, h->boxes, st);
+      h->boxes_valid = false;
       h->steps += 1;
       break;
     default:

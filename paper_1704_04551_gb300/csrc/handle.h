@@ -63,6 +63,7 @@ struct ibm_lbm {
   MarkerGroup* groups = nullptr;  // transfer blocks
   int n_groups = 0;
   int4* boxes = nullptr;          // per group: stencil box origin and size
+  bool boxes_valid = false;       // boxes match the markers' current positions (stage interface)
   bool need_zero_F = false;
   // state
   long long steps = 0;

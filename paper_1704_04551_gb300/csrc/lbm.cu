@@ -215,8 +215,14 @@ void launch_collide_g(const LatticeDev& L, const RowInfo* rows, int n_rows, bool
   const int ty = COLLIDE_THREADS / tx;
   const int nxb = (L.nx + tx - 1) / tx;
   const dim3 block(tx, ty), grid((unsigned)nxb * (unsigned)((n_rows + ty - 1) / ty));
-  // 32-bit element offsets in the odd step while 19 N < 2^32
+  // 32-bit element offsets in the odd step while 19 N < 2^32 (a build with
+  // IBM_FORCE_IDX64 defined always takes the 64-bit variant, so that the
+  // parity tests reach it on small lattices)
+#ifdef IBM_FORCE_IDX64
+  const bool idx32 = false;
+#else
   const bool idx32 = (unsigned long long)Q * (unsigned long long)L.N < (1ull << 32);
+#endif
   if (odd && idx32) {
     if (dense) k_collide<S, 1, GEOM, true, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);
     else k_collide<S, 1, GEOM, false, true><<<grid, block, 0, st>>>(L, rows, n_rows, nxb);

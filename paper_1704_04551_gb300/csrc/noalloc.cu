@@ -8,8 +8,6 @@
 // same as the SPREAD stage of a handle.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/ibm_lbm.h"
 #include "common.cuh"
 
@@ -21,25 +19,15 @@ namespace {
 // comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) float4 g_noalloc_scratch[IBM_LBM_NOALLOC_MAX_CELLS];
 
-constexpr int MAX_DEVICES = 64;
-float4* g_scratch_ptr[MAX_DEVICES] = {};
-std::mutex g_scratch_mutex;
-
-// Device address of the accumulator on the current device (looked up once
-// per device, with that device current).
+// Device address of the accumulator in the current context. Looked up on
+// every call (a host-side table lookup once the module is loaded) rather than
+// cached: if the caller resets the device, the module is loaded again and the
+// array may move, and a cached address would then point at freed memory.
 cudaError_t scratch_address(float4** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<float4*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<float4*>(p);
   return cudaSuccess;
 }
 
@@ -63,6 +51,11 @@ __global__ void k_spread_noalloc(Grid G, const double* __restrict__ X, const dou
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
   const double px = X[k], py = X[(size_t)M + k], pz = X[2 * (size_t)M + k];
+  // Positions come straight from device memory, unchecked by the host: a
+  // marker that is not finite or lies at |x| >= 2^30 (the bound the handle's
+  // set_markers enforces) is skipped, so that no index below overflows.
+  const double lim = 1073741824.0;
+  if (!(fabs(px) < lim && fabs(py) < lim && fabs(pz) < lim)) return;
   const float fx = (float)F[k], fy = (float)F[(size_t)M + k], fz = (float)F[2 * (size_t)M + k];
   const double bx = floor(px), by = floor(py), bz = floor(pz);
   const float ox = (float)(px - bx), oy = (float)(py - by), oz = (float)(pz - bz);
@@ -105,8 +98,9 @@ __global__ void k_scatter_noalloc(const float4* acc, int N, double* g) {
 }  // namespace
 }  // namespace ibm
 
-extern "C" int ibm_lbm_spread_noalloc(const double* X, const double* F, int64_t n_markers, int32_t nx, int32_t ny,
-                                      int32_t nz, int32_t geometry, double tube_radius, double* g, void* stream) {
+namespace {
+int spread_noalloc(const double* X, const double* F, int64_t n_markers, int32_t nx, int32_t ny, int32_t nz,
+                   int32_t geometry, double tube_radius, double* g, void* stream) {
   using namespace ibm;
   const long long N = (long long)nx * ny * nz;
   if (nx < 4 || ny < 4 || nz < 4 || N > IBM_LBM_NOALLOC_MAX_CELLS) return IBM_LBM_E_ARG;
@@ -129,4 +123,16 @@ extern "C" int ibm_lbm_spread_noalloc(const double* X, const double* F, int64_t 
   k_scatter_noalloc<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, (int)N, g);
   if (cudaGetLastError() != cudaSuccess) return IBM_LBM_E_CUDA;
   return IBM_LBM_OK;
+}
+}  // namespace
+
+// No C++ exception crosses the C ABI (there is no handle to carry a message).
+extern "C" int ibm_lbm_spread_noalloc(const double* X, const double* F, int64_t n_markers, int32_t nx, int32_t ny,
+                                      int32_t nz, int32_t geometry, double tube_radius, double* g,
+                                      void* stream) {
+  try {
+    return spread_noalloc(X, F, n_markers, nx, ny, nz, geometry, tube_radius, g, stream);
+  } catch (...) {
+    return IBM_LBM_E_ARG;
+  }
 }

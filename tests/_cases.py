@@ -46,3 +46,15 @@ def markers_inside(lat, M, seed):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def membrane_case(n=40, R=16.0, cells=3, seed=21, deform=0.08):
+    """Three red-cell membranes in a 40^3 tube, vertices displaced by
+    `deform` lu (Gaussian), with moduli stiffer than the physical ones so
+    that every force term is visible."""
+    w = I.rbc_tube(n=n, radius=R, n_cells=cells, seed=seed, steps=0)
+    rng = np.random.default_rng(seed + 1)
+    w['X'] = w['X'] + deform * rng.standard_normal(w['X'].shape)
+    for b in w['bodies']:
+        b.update(kBT_p=2e-3, k_b=1e-3, k_l=5e-3, k_g=4e-3, k_v=3e-3)
+    return w

@@ -21,7 +21,7 @@ import pytest
 
 import oracle as O
 from paper_1704_04551_gb300 import inputs as I
-from tests._cases import LATTICES, fluid_mask, markers_inside, rel_l2, shape
+from tests._cases import LATTICES, fluid_mask, markers_inside, membrane_case, rel_l2, shape
 
 pytestmark = pytest.mark.gpu
 
@@ -89,14 +89,7 @@ def test_interpolate_matches_oracle(cuda_lib, geom):
     assert np.abs(Xg - Xo).max() < 1e-6
 
 
-def _membrane_case(n=40, R=16.0, cells=3, seed=21, deform=0.08):
-    w = I.rbc_tube(n=n, radius=R, n_cells=cells, seed=seed, steps=0)
-    rng = np.random.default_rng(seed + 1)
-    w['X'] = w['X'] + deform * rng.standard_normal(w['X'].shape)
-    # stiffer moduli than the physical ones so that every term is visible
-    for b in w['bodies']:
-        b.update(kBT_p=2e-3, k_b=1e-3, k_l=5e-3, k_g=4e-3, k_v=3e-3)
-    return w
+_membrane_case = membrane_case
 
 
 def test_membrane_forces_match_oracle(cuda_lib):

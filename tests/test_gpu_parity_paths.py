@@ -1,0 +1,108 @@
+"""Kernel paths that the small coupled parity tests do not reach, each
+against the FP64 oracle through the C ABI:
+
+* the collide variant with 64-bit element offsets (taken when 19 N >= 2^32,
+  i.e. only above ~600^3 cells), from a build with IBM_FORCE_IDX64 that
+  selects it on small lattices (Sec. 2.1, Eqs. lbm, rho_u, Guo term);
+* the collide on a lattice wide enough for full 128-cell blocks, a ragged
+  x block and many row blocks, with a spread force density on touched
+  tiles, over even and odd steps;
+* the membrane force scatter in fixed point (taken once a previous step set
+  the body's scale) and its float redo (taken when a contribution outgrows
+  that scale) (Sec. 2.2, Eqs. membrane-potential .. volumeEnergy).
+Tolerances as in test_gpu_parity.py."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1704_04551_gb300 import inputs as I
+from tests._cases import membrane_case, shape
+from tests._collide_parity import check_collide_parity
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WIDE = {
+    'periodic': dict(nx=160, ny=40, nz=36, tau=0.8, geometry=0, body_force=[2e-6, -1e-6, 5e-7]),
+    'ywalls': dict(nx=160, ny=38, nz=36, tau=0.7, geometry=1, wall_u=[-0.015, 0.02], body_force=[1e-6, 0, 0]),
+    'tube': dict(nx=160, ny=40, nz=40, tau=1.0, geometry=2, tube_radius=18.5, body_force=[3e-6, 0, 0]),
+}
+
+
+def _tracers(lat, M, seed):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape(lat)
+    if lat['geometry'] == 2:
+        r = (lat['tube_radius'] - 1.0) * np.sqrt(rng.random(M))
+        th = 2 * np.pi * rng.random(M)
+        X = np.stack([nx * rng.random(M), (ny - 1) / 2 + r * np.cos(th), (nz - 1) / 2 + r * np.sin(th)])
+    else:
+        X = np.stack([nx * rng.random(M), (ny - 1) * rng.random(M), nz * rng.random(M)])
+    F = 2e-3 * (2 * rng.random((3, M)) - 1)
+    return X, F
+
+
+@pytest.mark.parametrize('geom', list(WIDE))
+def test_collide_wide_lattice_with_force_density(cuda_lib, geom):
+    lat = WIDE[geom]
+    check_collide_parity(cuda_lib, lat, steps=3, seed=13, markers=_tracers(lat, 3000, 14))
+
+
+def test_collide_64bit_offsets_variant(cuda_lib):
+    """The same collide parity on a library built with IBM_FORCE_IDX64, run
+    in a child process that loads that build."""
+    from paper_1704_04551_gb300 import build
+    out = os.path.join(build.BUILD, 'idx64', 'libibmlbm.so')
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    build.build(extra=['-DIBM_FORCE_IDX64'], out=out)
+    env = dict(os.environ, IBM_LBM_LIBRARY=out, PYTHONPATH=ROOT + os.pathsep + os.environ.get('PYTHONPATH', ''))
+    r = subprocess.run([sys.executable, '-m', 'tests._collide_parity'], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count(' ok ') == 3, r.stdout
+
+
+def test_membrane_forces_fixed_point_after_steps(cuda_lib):
+    """After three coupled steps every body has a scale from its previous
+    forces, so the FORCES stage scatters in fixed point; the result matches
+    the oracle's forces at the GPU's current positions."""
+    w = membrane_case()
+    w['lattice'] = dict(w['lattice'], body_force=[2e-6, 0, 0])
+    sim = cuda_lib.Simulation.from_workload(w)
+    sim.step(3)
+    Xg = sim.markers()[0]
+    ora = O.Oracle.from_workload(dict(w, X=Xg))
+    sim.stage(cuda_lib.STAGE_FORCES)
+    ora.stage_forces()
+    Fg, Fo = sim.markers()[2], ora.markers()[2]
+    scale = np.abs(Fo).max()
+    assert scale > 1e-5
+    assert np.abs(Fg - Fo).max() < 1e-4 * scale
+
+
+def test_membrane_forces_overflow_redo(cuda_lib):
+    """Bodies one step away from their rest shape set a tiny scale; a random
+    flow then displaces the vertices by ~1e-2 lu, so this step's
+    contributions exceed the fixed-point headroom by orders of magnitude
+    and every block redoes its scatter with float atomics."""
+    w = membrane_case(deform=1e-7)
+    sim = cuda_lib.Simulation.from_workload(w)
+    sim.step(1)
+    rng = np.random.default_rng(5)
+    u = 0.02 * (2 * rng.random((3, sim.N)) - 1)
+    sim.set_lattice(None, u)
+    sim.stage(cuda_lib.STAGE_SPREAD)   # stencil boxes at the current positions
+    sim.stage(cuda_lib.STAGE_INTERP)   # advect by the random flow
+    Xg = sim.markers()[0]
+    ora = O.Oracle.from_workload(dict(w, X=Xg))
+    sim.stage(cuda_lib.STAGE_FORCES)
+    ora.stage_forces()
+    Fg, Fo = sim.markers()[2], ora.markers()[2]
+    scale = np.abs(Fo).max()
+    assert scale > 1e-4
+    assert np.abs(Fg - Fo).max() < 1e-4 * scale
