@@ -67,7 +67,7 @@ __device__ __forceinline__ LatticeDev case_lattice(const CaseDev& C) {
   return L;
 }
 
-constexpr int SERVE_XFER_THREADS = 512;
+constexpr int SERVE_XFER_THREADS = XFER_THREADS;
 constexpr int SERVE_COLLIDE_TX = 32, SERVE_COLLIDE_TY = 4;
 
 __global__ void k_book_begin(CaseDev* cases, int n) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_spread_b(const CaseDe
 }
 
 __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_interpolate_b(const CaseDev* cases, const Item* items) {
-  extern __shared__ __align__(16) float fbox[];
+  extern __shared__ __align__(16) float4 fbox[];
   const Item it = items[blockIdx.x];
   const CaseDev& C = cases[it.c];
   if (!C.active) return;
@@ -411,14 +411,13 @@ int rebuild(ibm_lbm_server_t* s) {
   }
   cudaGraph_t g = nullptr;
   SCUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  const size_t box_smem = 3 * 8192 * sizeof(float);
   for (int step = 0; step < s->cfg.chunk_steps; ++step) {
     k_book_begin<<<(n + 127) / 128, 128, 0, s->stream>>>(s->d_cases, n);
     k_clear_flags<<<n, 256, 0, s->stream>>>(s->d_cases);
     if (s->n_rigid) k_rigid_b<<<s->n_rigid, RIGID_THREADS, 0, s->stream>>>(s->d_cases, s->d_rigid);
     if (s->n_membranes)
       k_membranes_b<<<s->n_membranes, MEMBRANE_THREADS, s->membrane_smem, s->stream>>>(s->d_cases, s->d_membranes);
-    if (s->n_groups) k_spread_b<<<s->n_groups, SERVE_XFER_THREADS, box_smem, s->stream>>>(s->d_cases, s->d_groups);
+    if (s->n_groups) k_spread_b<<<s->n_groups, SERVE_XFER_THREADS, SPREAD_SMEM, s->stream>>>(s->d_cases, s->d_groups);
     for (int g = 0; g < 3; ++g) {
       const int first = s->geom_first[g], n_items = s->geom_first[g + 1] - first;
       if (n_items == 0) continue;
@@ -437,7 +436,7 @@ int rebuild(ibm_lbm_server_t* s) {
       }
     }
     if (s->n_groups)
-      k_interpolate_b<<<s->n_groups, SERVE_XFER_THREADS, box_smem, s->stream>>>(s->d_cases, s->d_groups);
+      k_interpolate_b<<<s->n_groups, SERVE_XFER_THREADS, INTERP_SMEM, s->stream>>>(s->d_cases, s->d_groups);
     k_book_end<<<(n + 127) / 128, 128, 0, s->stream>>>(s->d_cases, n);
   }
   cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
@@ -513,9 +512,8 @@ static int impl_ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ib
     ibm_lbm_server_destroy(s);
     return IBM_LBM_E_NOMEM;
   }
-  const int smem = 3 * 8192 * (int)sizeof(float);
-  if (cudaFuncSetAttribute(k_spread_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_interpolate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_spread_b, cudaFuncAttributeMaxDynamicSharedMemorySize, SPREAD_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_interpolate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, INTERP_SMEM) != cudaSuccess) {
     cudaGetLastError();
     ibm_lbm_server_destroy(s);
     return IBM_LBM_E_CUDA;

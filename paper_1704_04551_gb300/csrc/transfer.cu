@@ -26,16 +26,16 @@ __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, Marker
 template <int GEOM>
 __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, MarkersDev m,
                                                                  const MarkerGroup* groups, const int4* boxes) {
-  extern __shared__ __align__(16) float box[];  // [3][vol]
-  interpolate_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, box);
+  extern __shared__ __align__(16) float4 vbox[];  // [vol] velocities
+  interpolate_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, vbox);
 }
 
 cudaError_t transfer_configure() {
   cudaError_t e = cudaSuccess;
-  const int smem = 3 * BOX_CELLS * (int)sizeof(float);
-#define CFG(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-  CFG(k_spread<GEOM_PERIODIC>); CFG(k_spread<GEOM_YWALLS>); CFG(k_spread<GEOM_TUBE>);
-  CFG(k_interpolate<GEOM_PERIODIC>); CFG(k_interpolate<GEOM_YWALLS>); CFG(k_interpolate<GEOM_TUBE>);
+#define CFG(k, smem) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+  CFG(k_spread<GEOM_PERIODIC>, SPREAD_SMEM); CFG(k_spread<GEOM_YWALLS>, SPREAD_SMEM); CFG(k_spread<GEOM_TUBE>, SPREAD_SMEM);
+  CFG(k_interpolate<GEOM_PERIODIC>, INTERP_SMEM); CFG(k_interpolate<GEOM_YWALLS>, INTERP_SMEM);
+  CFG(k_interpolate<GEOM_TUBE>, INTERP_SMEM);
 #undef CFG
   return e;
 }
@@ -63,7 +63,7 @@ void launch_stencil_cache(const MarkersDev& m, cudaStream_t st) {
 void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups, int4* boxes,
                    cudaStream_t st) {
   if (m.M == 0 || n_groups == 0) return;
-  const size_t smem = 3 * BOX_CELLS * sizeof(float);
+  const size_t smem = SPREAD_SMEM;
   switch (L.geometry) {
     case GEOM_PERIODIC: k_spread<GEOM_PERIODIC><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
     case GEOM_YWALLS: k_spread<GEOM_YWALLS><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
@@ -74,7 +74,7 @@ void launch_spread(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* 
 void launch_interpolate(const LatticeDev& L, const MarkersDev& m, const MarkerGroup* groups, int n_groups,
                         const int4* boxes, cudaStream_t st) {
   if (m.M == 0 || n_groups == 0) return;
-  const size_t smem = 3 * BOX_CELLS * sizeof(float);
+  const size_t smem = INTERP_SMEM;
   switch (L.geometry) {
     case GEOM_PERIODIC: k_interpolate<GEOM_PERIODIC><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;
     case GEOM_YWALLS: k_interpolate<GEOM_YWALLS><<<n_groups, XFER_THREADS, smem, st>>>(L, m, groups, boxes); break;

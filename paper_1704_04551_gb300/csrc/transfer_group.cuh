@@ -9,27 +9,33 @@
 // nodes floor(X)-1 .. floor(X)+2 on each axis; nodes inside walls or the
 // tube's solid are skipped (no renormalisation). Periodic axes wrap.
 //
+// Delta weights: with f = X - floor(X) in [0, 1) and t = pi f / 2, the four
+// nodes sit at r = -1-f, -f, 1-f, 2-f, where cos(pi r / 2) is -sin t,
+// cos t, sin t, -cos t. One sine/cosine pair per axis gives all four
+// weights: (1 - sin t)/4, (1 + cos t)/4, (1 + sin t)/4, (1 - cos t)/4.
+//
 // Positions are FP64, but these kernels read the per-marker stencil cache
 // (floor(X) as integers, X - floor(X) rounded once to FP32), which the
 // interpolation kernel refreshes right after advecting each marker; the only
 // FP64 arithmetic left is that advection.
 //
-// One thread block per marker group (a body, or a run of tracers), four
-// threads per marker: lane a handles the stencil's x offset a, so the four
-// read or write consecutive words, and the y/z weights are computed once and
-// shared by shuffles. The block bounds the group's stencils with a box; when
-// the box fits in shared memory (BOX_CELLS cells):
+// One thread block per marker group (a body, or a run of tracers), one
+// thread per marker: a thread computes its marker's 12 weights once and
+// visits the 64 stencil nodes itself. The block bounds the group's stencils
+// with a box; when the box fits in shared memory (BOX_CELLS cells):
 //   spreading accumulates there in 32-bit fixed point (native integer
 //   shared-memory atomics; the sum does not depend on the order of the
 //   additions) with a scale chosen from the group's largest force so that no
 //   cell can overflow, then adds the box's nonzero cells to global memory
 //   (one float4 atomic each);
-//   interpolation loads the box of velocities once and gathers from shared
-//   memory.
+//   interpolation loads the box of velocities (float4 per cell, so that one
+//   16-byte shared load serves a node) once and gathers from shared memory;
+//   the same sweep clears the force density the collision has consumed.
 // Larger boxes (scattered tracers, very large bodies) fall back to
 // per-marker global float4 atomics / gathers. The box of each group is
 // computed by the spread kernel and reused by the interpolation of the same
-// step (markers do not move in between).
+// step (markers do not move in between; a marker found outside the box
+// takes the per-marker path).
 #pragma once
 #include <climits>
 
@@ -39,48 +45,35 @@ namespace ibm {
 
 namespace xfer_detail {
 
-constexpr int XFER_THREADS = 512;   // two blocks per SM (shared-memory box), 32 warps
-constexpr int BOX_CELLS = 8192;     // 3 words per cell: 96 KiB of shared memory
+constexpr int XFER_THREADS = 352;   // 11 warps: a 642-vertex body is two passes at 91 % of the lanes
+constexpr int BOX_CELLS = 6144;     // shared-memory box limit (cells)
+constexpr int SPREAD_SMEM = 3 * BOX_CELLS * (int)sizeof(int);     // fixed-point sums, [3][vol]
+constexpr int INTERP_SMEM = BOX_CELLS * (int)sizeof(float4);      // velocities, [vol] float4
 
-__device__ __forceinline__ float phi(float r) { return 0.25f * (1.0f + cospif(0.5f * r)); }
-
-// Stencil of marker k as seen by lane a of its 4-lane group: first node
-// (unwrapped) on each axis, this lane's x weight and the four y and z
-// weights (computed one per lane and shared by shuffles). All 32 lanes of
-// the warp must call this (inactive groups pass any valid k).
-struct LaneStencil {
-  int bx, by, bz;
-  float wx;           // weight of node bx + a
-  float wy[4], wz[4];
-};
-// The stencil cache of one marker as read from global memory (the
-// interpolation loads the next pass's entries while the current pass
-// gathers, so that a pass does not wait for its own loads).
-struct RawStencil {
-  int c[3];
-  float f[3];
-};
-__device__ __forceinline__ void load_raw(const MarkersDev& m, int k, RawStencil& r) {
-  const size_t M = (size_t)m.M;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    r.c[q] = m.cell[q * M + k];
-    r.f[q] = m.frac[q * M + k];
-  }
+// The four delta weights of one axis for a marker at fractional offset f.
+__device__ __forceinline__ void axis_weights(float f, float w[4]) {
+  float s, c;
+  sincospif(0.5f * f, &s, &c);
+  w[0] = fmaf(-0.25f, s, 0.25f);
+  w[1] = fmaf(0.25f, c, 0.25f);
+  w[2] = fmaf(0.25f, s, 0.25f);
+  w[3] = fmaf(-0.25f, c, 0.25f);
 }
-__device__ __forceinline__ void lane_stencil(const RawStencil& r, int a, LaneStencil& s) {
-  s.bx = r.c[0] - 1;
-  s.by = r.c[1] - 1;
-  s.bz = r.c[2] - 1;
-  // node b + a sits at distance (a - 1) - frac from X
-  s.wx = phi((float)(a - 1) - r.f[0]);
-  const float wy_own = phi((float)(a - 1) - r.f[1]), wz_own = phi((float)(a - 1) - r.f[2]);
-  const int base = threadIdx.x & 28;  // first lane of this 4-lane group within the warp
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    s.wy[b] = __shfl_sync(0xffffffffu, wy_own, base + b);
-    s.wz[b] = __shfl_sync(0xffffffffu, wz_own, base + b);
-  }
+
+// Stencil of one marker: first node (unwrapped) on each axis and the
+// weights of its four nodes per axis.
+struct Stencil {
+  int bx, by, bz;
+  float wx[4], wy[4], wz[4];
+};
+__device__ __forceinline__ void load_stencil(const MarkersDev& m, int k, Stencil& s) {
+  const size_t M = (size_t)m.M;
+  s.bx = m.cell[k] - 1;
+  s.by = m.cell[M + k] - 1;
+  s.bz = m.cell[2 * M + k] - 1;
+  axis_weights(m.frac[k], s.wx);
+  axis_weights(m.frac[M + k], s.wy);
+  axis_weights(m.frac[2 * M + k], s.wz);
 }
 
 // wrap / range handling of a stencil row (y, z) for the geometry; false if
@@ -113,8 +106,8 @@ __device__ __forceinline__ int axis_tiles(int b, int n, int sh, int t[2]) {
 
 // Mark the (at most 8) tiles covered by a marker's stencil. Markers of a
 // group are numbered along a space-filling curve, so a marker whose tile set
-// equals that of the marker handled by the previous 4-lane group of the warp
-// skips its stores.
+// equals that of the previous lane's marker skips its stores. All 32 lanes
+// of the warp call this.
 template <int GEOM>
 __device__ __forceinline__ void mark_tiles(const LatticeDev& L, int bx, int by, int bz, bool active) {
   int tx[2] = {-1, -1}, ty[2] = {-1, -1}, tz[2] = {-1, -1};
@@ -123,14 +116,13 @@ __device__ __forceinline__ void mark_tiles(const LatticeDev& L, int bx, int by, 
                                         : axis_tiles<false>(by, L.ny, TILE_Y_SHIFT, ty);
   const int nz_ = GEOM != GEOM_TUBE ? axis_tiles<true>(bz, L.nz, TILE_Z_SHIFT, tz)
                                     : axis_tiles<false>(bz, L.nz, TILE_Z_SHIFT, tz);
-  // same tile set as the previous 4-lane group in the warp?
-  const int src = ((int)(threadIdx.x & 31) - 4) & 31;
-  bool same = __shfl_sync(0xffffffffu, (int)active, src) != 0 && (threadIdx.x & 31) >= 4;
+  const int lane = threadIdx.x & 31;
+  bool same = __shfl_up_sync(0xffffffffu, (int)active, 1) != 0 && lane >= 1;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    same &= __shfl_sync(0xffffffffu, tx[q], src) == tx[q];
-    same &= __shfl_sync(0xffffffffu, ty[q], src) == ty[q];
-    same &= __shfl_sync(0xffffffffu, tz[q], src) == tz[q];
+    same &= __shfl_up_sync(0xffffffffu, tx[q], 1) == tx[q];
+    same &= __shfl_up_sync(0xffffffffu, ty[q], 1) == ty[q];
+    same &= __shfl_up_sync(0xffffffffu, tz[q], 1) == tz[q];
   }
   if (!active || same) return;
   for (int c = 0; c < nz_; ++c)
@@ -230,12 +222,12 @@ __device__ inline void group_box(const MarkersDev& m, const MarkerGroup& G, int4
   fmax = __uint_as_float(s_fmax);
 }
 
-// Round-to-nearest-even of |v| <= 2^22 to an integer with one full-rate add:
-// v + 1.5 * 2^23 has a fixed exponent, so its low mantissa bits hold
-// round(v) + 2^22 (the float-to-int conversion unit runs at a quarter of the
-// FP32 rate).
-__device__ __forceinline__ int to_fixed(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
-
+// round(a * b) for |a b| <= 2^22, with one fused multiply-add: a b + 1.5 2^23
+// has a fixed exponent, so its low mantissa bits hold round(a b) + 2^22
+// (the float-to-int conversion unit runs at a quarter of the FP32 rate).
+__device__ __forceinline__ int fixed_mul(float a, float b) {
+  return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
+}
 
 // Lane mapping of a row-by-row sweep over a box whose rows hold dx cells:
 // rows shorter than a warp are packed rpw to a warp (lane -> sub-row sub,
@@ -258,11 +250,52 @@ __device__ __forceinline__ RowSweep row_sweep(int dx) {
   return w;
 }
 
+// Row r of a box with dy rows per z layer as (iy, iz), without an integer
+// division: for 0 <= r < BOX_CELLS the float quotient (r + 1/2)/dy lies at
+// least 1/(2 dy) from an integer, far beyond its rounding error.
+__device__ __forceinline__ void row_yz(int r, int dy, float inv_dy, int& iy, int& iz) {
+  iz = (int)(((float)r + 0.5f) * inv_dy);
+  iy = r - iz * dy;
+}
+
+// Wrapped x of box column ax (box origin x0 already wrapped into [0, nx)).
+__device__ __forceinline__ int box_x(int xw0, int ax, int nx) {
+  const int x = xw0 + ax;
+  if (x < nx) return x;
+  return (ax < nx) ? x - nx : wrapi(x, nx);
+}
+
 }  // namespace xfer_detail
 using namespace xfer_detail;
 
+// Force of one marker added to the lattice with global float4 atomics
+// (groups whose box does not fit in shared memory). Kept out of line: it is
+// the rare path.
+template <int GEOM>
+__device__ __noinline__ void scatter_global(const LatticeDev& L, const Stencil& s, float4 F) {
+  int xs[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) xs[a] = wrapi(s.bx + a, L.nx);
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+      int y = s.by + b, z = s.bz + c;
+      if (!fluid_row<GEOM>(L, y, z)) continue;
+      const float wyz = s.wy[b] * s.wz[c];
+      float4* row = L.g + (size_t)L.nx * (y + L.ny * z);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float w = s.wx[a] * wyz;
+        atomicAdd(row + xs[a], make_float4(F.x * w, F.y * w, F.z * w, 0.f));
+      }
+    }
+  }
+}
+
 // Spreading of one marker group by the whole thread block; box_out receives
 // the group's stencil box (origin, size) for the interpolation of this step.
+// ibox: [3][BOX_CELLS] ints of shared memory.
 template <int GEOM>
 __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
                                              int4* box_out, int* ibox) {
@@ -277,73 +310,71 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   const bool in_smem = dims.w != 0;
   // touched tiles: from the box when it fits, else marker by marker below
   if (in_smem) mark_box_tiles<GEOM>(L, lo, dims);
+  if (in_smem && !any_force) return;
   const int vol = dims.x * dims.y * dims.z;
   // Fixed-point scale: a contribution is at most fmax / 8 (delta <= 1/8) and
   // a cell's sum at most count * fmax / 8; S keeps contributions below 2^22
-  // (converted exactly by to_fixed) and sums below 2^30.
+  // (converted exactly by fixed_mul) and sums below 2^30.
   const float S = any_force ? fminf(33554432.0f, 8589934592.0f / (float)G.count) / fmax : 0.f;
-  if (in_smem && any_force) {
+  if (in_smem) {
     for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
     __syncthreads();
   }
-  const int a = threadIdx.x & 3;
-  // whole warps iterate together (shuffles inside)
-  for (int j0 = 0; j0 < G.count; j0 += blockDim.x >> 2) {
-    if (j0 + ((threadIdx.x >> 5) << 3) >= G.count) continue;  // the whole warp is past the group's end
-    if (in_smem && !any_force) break;
-    const int j = j0 + (threadIdx.x >> 2);
+  // one thread per marker; whole warps iterate together (shuffles in mark_tiles)
+  for (int j0 = 0; j0 < G.count; j0 += blockDim.x) {
+    if (j0 + (int)(threadIdx.x & ~31u) >= G.count) break;  // the whole warp is past the group's end
+    const int j = j0 + threadIdx.x;
     const bool active = j < G.count;
     const int k = G.first + (active ? j : 0);
-    RawStencil r;
-    load_raw(m, k, r);
-    LaneStencil s;
-    lane_stencil(r, a, s);
-    if (!in_smem) mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active && a == 0);
+    Stencil s;
+    load_stencil(m, k, s);
+    if (!in_smem) mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active);
     if (!active || !any_force) continue;
     const float4 F = m.F[k];
     if (in_smem) {
-      const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
-      const float fx = F.x * S * s.wx, fy = F.y * S * s.wx, fz = F.z * S * s.wx;
+      float fx[4], fy[4], fz[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        fx[a] = F.x * S * s.wx[a];
+        fy[a] = F.y * S * s.wx[a];
+        fz[a] = F.z * S * s.wx[a];
+      }
+      const int li0 = (s.bx - lo.x) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const float w = s.wy[b] * s.wz[c];
-          const int li = li0 + dims.x * (b + dims.y * c);
-          atomicAdd(ibox + li, to_fixed(fx * w));
-          atomicAdd(ibox + vol + li, to_fixed(fy * w));
-          atomicAdd(ibox + 2 * vol + li, to_fixed(fz * w));
+          int* p = ibox + li0 + dims.x * (b + dims.y * c);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            atomicAdd(p + a, fixed_mul(fx[a], w));
+            atomicAdd(p + vol + a, fixed_mul(fy[a], w));
+            atomicAdd(p + 2 * vol + a, fixed_mul(fz[a], w));
+          }
         }
     } else {
-      const int x = wrapi(s.bx + a, L.nx);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int y = s.by + b, z = s.bz + c;
-          if (!fluid_row<GEOM>(L, y, z)) continue;
-          const float w = s.wx * s.wy[b] * s.wz[c];
-          atomicAdd(L.g + L.nx * (y + L.ny * z) + x, make_float4(F.x * w, F.y * w, F.z * w, 0.f));
-        }
-      }
+      scatter_global<GEOM>(L, s, F);
     }
   }
-  if (!in_smem || !any_force) return;
+  if (!in_smem) return;
   __syncthreads();
   // add the nonzero cells of the box to the lattice, row by row
   const float inv = 1.0f / S;
   const int nrows = dims.y * dims.z;
   const int nwarps = blockDim.x >> 5;
   const RowSweep sw = row_sweep(dims.x);
+  const float inv_dy = 1.0f / (float)dims.y;
   const int xw0 = wrapi(lo.x, L.nx);
   for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
-    int x = xw0 + ax;
-    if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+    const int x = box_x(xw0, ax, L.nx);
     for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += nwarps * sw.rpw) {
       const int li = r * dims.x + ax;
       const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
       if ((qx | qy | qz) == 0) continue;
-      int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
+      int iy, iz;
+      row_yz(r, dims.y, inv_dy, iy, iz);
+      int y = lo.y + iy, z = lo.z + iz;
       if (!fluid_row<GEOM>(L, y, z)) continue;
       atomicAdd(L.g + (size_t)L.nx * (y + L.ny * z) + x,
                 make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
@@ -351,42 +382,72 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   }
 }
 
+// Velocity at one marker gathered from the lattice (groups whose box does
+// not fit in shared memory, or a marker outside its group's box); with
+// clear, the visited cells' force density is reset (consumed by the
+// collision). Kept out of line: it is the rare path.
+template <int GEOM>
+__device__ __noinline__ float3 gather_global(const LatticeDev& L, const Stencil& s, bool clear) {
+  int xs[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) xs[a] = wrapi(s.bx + a, L.nx);
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+      int y = s.by + b, z = s.bz + c;
+      if (!fluid_row<GEOM>(L, y, z)) continue;
+      const size_t rb = (size_t)L.nx * (y + L.ny * z);
+      float rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4 v = L.uw[rb + xs[a]];
+        if (clear) L.g[rb + xs[a]] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rx = fmaf(s.wx[a], v.x, rx);
+        ry = fmaf(s.wx[a], v.y, ry);
+        rz = fmaf(s.wx[a], v.z, rz);
+      }
+      const float w = s.wy[b] * s.wz[c];
+      ux = fmaf(w, rx, ux);
+      uy = fmaf(w, ry, uy);
+      uz = fmaf(w, rz, uz);
+    }
+  }
+  return make_float3(ux, uy, uz);
+}
+
 // Interpolation and advection of one marker group by the whole thread block.
+// vbox: [BOX_CELLS] float4 of shared memory.
 template <int GEOM>
 __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
-                                                  const int4* box_in, float* box) {
+                                                  const int4* box_in, float4* vbox) {
   const int4 lo = box_in[0], dims = box_in[1];
   const size_t M = (size_t)m.M;
   const bool in_smem = dims.w != 0;
-  const int vol = dims.x * dims.y * dims.z;
-  const int a = threadIdx.x & 3;
-  const int pass = blockDim.x >> 2;            // markers per pass
-  const int slot = threadIdx.x >> 2;           // this lane's marker within a pass
-  const int wfirst = (threadIdx.x >> 5) << 3;  // first marker of this warp within a pass
   const bool moves = !(G.flags & GROUP_FIXED);
-  // the first pass's stencil cache is loaded while the velocity box is
-  RawStencil nxt;
-  if (wfirst < G.count) load_raw(m, G.first + (slot < G.count ? slot : 0), nxt);
   if (in_smem) {
-    // load the box of velocities row by row; solid rows contribute zero
-    // one warp per box row, four rows in flight per lane (the loads are
-    // latency-bound: the rows are short)
+    // load the box of velocities row by row (solid rows read as zero) and
+    // clear the force density there, four rows in flight per lane (the
+    // loads are latency-bound: the rows are short)
     constexpr int RIF = 4;
     const int nrows = dims.y * dims.z;
     const int nwarps = blockDim.x >> 5;
     const RowSweep sw = row_sweep(dims.x);
     const int rstep = nwarps * sw.rpw;
+    const float inv_dy = 1.0f / (float)dims.y;
     const int xw0 = wrapi(lo.x, L.nx);
     for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
-      int x = xw0 + ax;
-      if (x >= L.nx) x = (ax < L.nx) ? x - L.nx : wrapi(x, L.nx);
+      const int x = box_x(xw0, ax, L.nx);
       for (int r0 = (threadIdx.x >> 5) * sw.rpw + sw.sub; r0 < nrows; r0 += RIF * rstep) {
         float4 u[RIF];
 #pragma unroll
         for (int q = 0; q < RIF; ++q) {
           const int r = r0 + q * rstep;
           u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          int y = lo.y + r % dims.y, z = lo.z + r / dims.y;
+          int iy, iz;
+          row_yz(r, dims.y, inv_dy, iy, iz);
+          int y = lo.y + iy, z = lo.z + iz;
           if (r < nrows && fluid_row<GEOM>(L, y, z)) {
             const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
             u[q] = L.uw[gi];
@@ -396,80 +457,52 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
 #pragma unroll
         for (int q = 0; q < RIF; ++q) {
           const int r = r0 + q * rstep;
-          if (r >= nrows) continue;
-          const int li = r * dims.x + ax;
-          box[li] = u[q].x;
-          box[vol + li] = u[q].y;
-          box[2 * vol + li] = u[q].z;
+          if (r < nrows) vbox[r * dims.x + ax] = u[q];
         }
       }
     }
     __syncthreads();
   }
-  // whole warps iterate together (shuffles inside); a warp stops at the
-  // first pass that lies entirely past the group's end
-  for (int j0 = 0; j0 + wfirst < G.count; j0 += pass) {
-    const int j = j0 + slot;
-    const bool active = j < G.count;
-    const int k = G.first + (active ? j : 0);
-    // this lane's coordinate (advection) and the next pass's stencil cache
-    // are loaded before the gather
-    const size_t off = (size_t)a * M + k;
-    double Xo = 0.0;
-    if (active && moves && a < 3) Xo = m.X[off];
-    const RawStencil cur = nxt;
-    if (j0 + pass + wfirst < G.count) {
-      const int jn = j + pass;
-      load_raw(m, G.first + (jn < G.count ? jn : 0), nxt);
-    }
-    LaneStencil s;
-    lane_stencil(cur, a, s);
+  for (int j = threadIdx.x; j < G.count; j += blockDim.x) {
+    const int k = G.first + j;
+    Stencil s;
+    load_stencil(m, k, s);
     float ux = 0.f, uy = 0.f, uz = 0.f;
-    if (in_smem) {
-      const int li0 = (s.bx - lo.x + a) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
+    const int ox = s.bx - lo.x, oy = s.by - lo.y, oz = s.bz - lo.z;
+    const bool inside = in_smem && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y &&
+                        oz + 4 <= dims.z;
+    if (inside) {
+      const int li0 = ox + dims.x * (oy + dims.y * oz);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
+          const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
+          const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
+          const float rx = fmaf(s.wx[3], v3.x, fmaf(s.wx[2], v2.x, fmaf(s.wx[1], v1.x, s.wx[0] * v0.x)));
+          const float ry = fmaf(s.wx[3], v3.y, fmaf(s.wx[2], v2.y, fmaf(s.wx[1], v1.y, s.wx[0] * v0.y)));
+          const float rz = fmaf(s.wx[3], v3.z, fmaf(s.wx[2], v2.z, fmaf(s.wx[1], v1.z, s.wx[0] * v0.z)));
           const float w = s.wy[b] * s.wz[c];
-          const int li = li0 + dims.x * (b + dims.y * c);
-          ux = fmaf(w, box[li], ux);
-          uy = fmaf(w, box[vol + li], uy);
-          uz = fmaf(w, box[2 * vol + li], uz);
+          ux = fmaf(w, rx, ux);
+          uy = fmaf(w, ry, uy);
+          uz = fmaf(w, rz, uz);
         }
     } else {
-      const int x = wrapi(s.bx + a, L.nx);
+      const float3 u = gather_global<GEOM>(L, s, !in_smem);
+      ux = u.x;
+      uy = u.y;
+      uz = u.z;
+    }
+    m.U[k] = make_float4(ux, uy, uz, 0.f);
+    if (moves) {
+      // advection (FP64), then the stencil cache of the new position
+      const float ua[3] = {ux, uy, uz};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int y = s.by + b, z = s.bz + c;
-          if (!fluid_row<GEOM>(L, y, z)) continue;
-          const float w = s.wy[b] * s.wz[c];
-          const float4 u = L.uw[L.nx * (y + L.ny * z) + x];
-          L.g[L.nx * (y + L.ny * z) + x] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed by the collision
-          ux = fmaf(w, u.x, ux);
-          uy = fmaf(w, u.y, uy);
-          uz = fmaf(w, u.z, uz);
-        }
+      for (int a = 0; a < 3; ++a) {
+        const double Xn = m.X[a * M + k] + (double)ua[a];
+        m.X[a * M + k] = Xn;
+        cache_coord(m, a * M + k, Xn);
       }
-    }
-    ux *= s.wx; uy *= s.wx; uz *= s.wx;
-    // sum the four x columns of the stencil
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-      ux += __shfl_xor_sync(0xffffffffu, ux, o);
-      uy += __shfl_xor_sync(0xffffffffu, uy, o);
-      uz += __shfl_xor_sync(0xffffffffu, uz, o);
-    }
-    if (!active) continue;
-    if (a == 0) m.U[k] = make_float4(ux, uy, uz, 0.f);
-    if (a < 3 && moves) {
-      // advection of one coordinate per lane (FP64), then its stencil cache
-      const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
-      const double Xn = Xo + (double)ua;
-      m.X[off] = Xn;
-      cache_coord(m, off, Xn);
     }
   }
 }
