@@ -19,12 +19,17 @@ _LIB = os.path.join(_HERE, 'liboracle.so')
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    """Compile the oracle with gcc (plain C, -O2, no fast-math), with OpenMP
+    over its independent loops (lattice z slabs, markers, bodies) when the
+    compiler has it; the results do not depend on the thread count."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(__file__))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f'.{os.getpid()}.tmp'
-        subprocess.check_call(['gcc', '-O2', '-std=c11', '-D_DEFAULT_SOURCE', '-fPIC', '-shared',
-                               '-o', tmp, _SRC, '-lm'])
+        base = ['gcc', '-O2', '-std=c11', '-D_DEFAULT_SOURCE', '-fPIC', '-shared', '-o', tmp, _SRC, '-lm']
+        try:
+            subprocess.check_call(base[:1] + ['-fopenmp'] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,6 +78,8 @@ def lib():
                      'ora_stage_interpolate'):
             getattr(L, name).argtypes = [P]
         L.ora_step.argtypes = [P, C.c_int64]
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_set_threads.restype = C.c_int
         L.ora_solid_steps.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_double, P, P]
         L.ora_phi.restype = C.c_double
         L.ora_phi.argtypes = [C.c_double]
@@ -105,6 +112,12 @@ def _f64(a):
 
 
 # ---------------------------------------------------------------- pure helpers
+def set_threads(n: int = 0) -> int:
+    """Threads the oracle's loops use (n <= 0: leave as is); returns the
+    count in effect (1 without OpenMP)."""
+    return int(lib().ora_set_threads(int(n)))
+
+
 def phi(r: float) -> float:
     return lib().ora_phi(float(r))
 

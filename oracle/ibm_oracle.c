@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 
@@ -256,6 +259,8 @@ void ora_stage_collide_stream(ora_t* o) {
   int64_t N = o->N;
   double tau = c->tau;
   memset(o->fn, 0, sizeof(double) * Q * N);
+  /* every destination slot has one source cell: the z slabs are independent */
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < c->nz; ++z)
     for (int y = 0; y < c->ny; ++y)
       for (int x = 0; x < c->nx; ++x) {
@@ -324,6 +329,8 @@ void ora_stage_interpolate(ora_t* o) {
   for (int b = 0; b < o->nb; ++b)
     if (o->bodies[b].kind == 3)
       for (int64_t k = o->bodies[b].first; k < o->bodies[b].first + o->bodies[b].count; ++k) fixed[k] = 1;
+  /* markers are independent */
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < M; ++k) {
     double X[3] = {o->X[k], o->X[M + k], o->X[2 * M + k]};
     int base[3];
@@ -829,6 +836,8 @@ void ora_morse_forces(const ora_t* o, const double* X, double* F) {
 void ora_stage_forces(ora_t* o) {
   int64_t M = o->M;
   memset(o->F, 0, sizeof(double) * 3 * (M ? M : 1));
+  /* each body writes only its own markers' forces and its own record */
+#pragma omp parallel for schedule(dynamic, 4)
   for (int b = 0; b < o->nb; ++b) {
     ora_body* B = &o->bodies[b];
     if (B->kind == 1) {
@@ -884,6 +893,16 @@ void ora_solid_steps(ora_t* o, int64_t n, double dt, double gamma, double mass, 
       v[i] = (v[i] + 0.5 * dt * F / mass) / (1.0 + 0.5 * gamma * dt);
     }
   }
+}
+
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 void ora_step(ora_t* o, int64_t n) {

@@ -105,6 +105,10 @@ void ora_filament_forces(const ora_t* o, int32_t b, const double* X, double* F);
 void ora_set_morse(ora_t* o, double D0, double alpha, double r0, double rc);
 double ora_morse_energy(const ora_t* o, const double* X);
 void ora_morse_forces(const ora_t* o, const double* X, double* F);
+/* Threads of the OpenMP loops (lattice z slabs, markers, bodies; the
+ * results do not depend on it); n <= 0 leaves the count unchanged. Returns
+ * the count in effect, 1 in a build without OpenMP. */
+int ora_set_threads(int n);
 /* Rest-state quantities derived from the template: A0, V0, mean l0. */
 void ora_mesh_rest(const ora_t* o, double out[3]);
 /* Shear modulus of the WLC-POW network (Eq. shearModulus). */

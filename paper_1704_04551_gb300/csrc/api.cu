@@ -19,8 +19,12 @@
 #include "common.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "transfer_group.cuh"
 
 using namespace ibm;
+
+static_assert(BODY_GROUP <= XFER_GROUP_MAX && TRACER_GROUP <= XFER_GROUP_MAX,
+              "transfer groups must fit the shared-memory marker records");
 
 namespace {
 
@@ -888,6 +892,41 @@ static int set_markers_into(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bo
       pos = B.first + B.count;
     }
     add_run(pos, n_markers, TRACER_GROUP, 0);
+    // Transfer blocks in the order of a Morton curve through the groups'
+    // mean positions (cells / 8 per axis, periodic x wrapped): blocks that
+    // run close in time then work on neighbouring cells, so the overlapping
+    // parts of their boxes are served from L2 rather than HBM.
+    {
+      const double nxd = (double)h->cfg.nx;
+      auto spread_bits = [](uint32_t v) {  // 10 bits -> every third of 30
+        uint64_t x = v & 0x3ffu;
+        x = (x | (x << 16)) & 0x30000ffull;
+        x = (x | (x << 8)) & 0x300f00full;
+        x = (x | (x << 4)) & 0x30c30c3ull;
+        x = (x | (x << 2)) & 0x9249249ull;
+        return x;
+      };
+      std::vector<std::pair<uint64_t, size_t>> key(groups.size());
+      for (size_t g = 0; g < groups.size(); ++g) {
+        double c[3] = {0.0, 0.0, 0.0};
+        for (int k = groups[g].first; k < groups[g].first + groups[g].count; ++k)
+          for (int a = 0; a < 3; ++a) c[a] += X[a * (size_t)M + k];
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) {
+          double v = c[a] / (double)groups[g].count;
+          if (a == 0) v -= nxd * std::floor(v / nxd);
+          q[a] = (uint32_t)std::min(1023.0, std::max(0.0, v / 8.0));
+        }
+        key[g] = {spread_bits(q[0]) | (spread_bits(q[1]) << 1) | (spread_bits(q[2]) << 2), g};
+      }
+      std::stable_sort(key.begin(), key.end(),
+                       [](const std::pair<uint64_t, size_t>& a, const std::pair<uint64_t, size_t>& b) {
+                         return a.first < b.first;
+                       });
+      std::vector<MarkerGroup> ordered(groups.size());
+      for (size_t g = 0; g < groups.size(); ++g) ordered[g] = groups[key[g].second];
+      groups.swap(ordered);
+    }
     h->n_groups = (int)groups.size();
     if ((rc = upload<MarkerGroup>(h, h->marker_mem, &h->groups, groups.data(), groups.size()))) return rc;
     h->boxes = (int4*)dalloc(h, h->marker_mem, sizeof(int4) * 2 * std::max<size_t>(1, groups.size()));
