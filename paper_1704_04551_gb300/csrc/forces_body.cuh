@@ -16,7 +16,10 @@
 // cache (floor(X) as integers, X - floor(X) rounded once to FP32): the
 // difference of two vertices is (floor_a - floor_b) + (frac_a - frac_b),
 // accurate to FP32 rounding of the difference itself, with no FP64
-// arithmetic (slow on this GPU). All force arithmetic is FP32; the body's
+// arithmetic (slow on this GPU). The integer parts are kept in shared memory
+// as floats relative to the body's first vertex (exact, and no conversion
+// per difference). All force arithmetic is FP32, with the approximate
+// division (2 ulp) where the quotient only scales a force; the body's
 // total area and volume are reduced in FP64. The volume gradient at a vertex
 // uses the closed-surface form dV/dx_v = (1/6) sum_{t at v} N_t (N_t the
 // triangle's doubled-area normal), which equals (1/6) sum x_{v+1} x x_{v+2}
@@ -94,18 +97,19 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
   const float kBT_p = Bp->kBT_p, k_b = Bp->k_b, k_l = Bp->k_l, k_g = Bp->k_g, k_v = Bp->k_v;
   const float q_prev = Bp->qmax;
-  int* sI = reinterpret_cast<int*>(smem);             // [3][nv] floor(X)
-  float* sR = reinterpret_cast<float*>(sI + 3 * nv);  // [3][nv] X - floor(X)
+  float* sI = reinterpret_cast<float*>(smem);         // [3][nv] floor(X) - floor(X_0), exact
+  float* sR = sI + 3 * nv;                            // [3][nv] X - floor(X)
   int* sQ = reinterpret_cast<int*>(sR + 3 * nv);      // [3][nv] force sums (fixed point, or float bits)
   float* sN = reinterpret_cast<float*>(sQ + 3 * nv);  // [3][nt] doubled-area normals
   float* sA = sN + 3 * nt;                            // [nt] areas
   __shared__ float s_dev[2];
   __shared__ unsigned s_qmax;
   const int first = Bp->first;
+  const int c0[3] = {m.cell[first], m.cell[M + first], m.cell[2 * M + first]};
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      sI[a * nv + v] = m.cell[a * M + first + v];
+      sI[a * nv + v] = (float)(m.cell[a * M + first + v] - c0[a]);
       sR[a * nv + v] = m.frac[a * M + first + v];
       sQ[a * nv + v] = 0;
     }
@@ -114,9 +118,8 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   __syncthreads();
   // x_a - x_b, exact in the integer part, one FP32 rounding in the fraction
   auto dv = [&](int a, int b) {
-    return make_float3((float)(sI[a] - sI[b]) + (sR[a] - sR[b]),
-                       (float)(sI[nv + a] - sI[nv + b]) + (sR[nv + a] - sR[nv + b]),
-                       (float)(sI[2 * nv + a] - sI[2 * nv + b]) + (sR[2 * nv + a] - sR[2 * nv + b]));
+    return make_float3((sI[a] - sI[b]) + (sR[a] - sR[b]), (sI[nv + a] - sI[nv + b]) + (sR[nv + a] - sR[nv + b]),
+                       (sI[2 * nv + a] - sI[2 * nv + b]) + (sR[2 * nv + a] - sR[2 * nv + b]));
   };
   auto normal = [&](int t) { return make_float3(sN[t], sN[nt + t], sN[2 * nt + t]); };
 
@@ -182,10 +185,11 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       }
       const float3 ev = dv(E.y, E.x);  // b - a
       const float L2 = dot(ev, ev), l = sqrtf(L2);
-      const float l0 = rest.x, x = l / (2.0f * l0);
+      const float rL2 = __fdividef(1.0f, L2), rl = l * rL2;
+      const float l0 = rest.x, x = __fdividef(l, 2.0f * l0);
       const float kp = 1.25f * kBT_p * l0 * l0;  // zero bond force at x = 1/2
-      const float dUdl = kBT_p * (0.25f / ((1.0f - x) * (1.0f - x)) - 0.25f + x) - kp / L2;
-      const float3 fs = (dUdl / l) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
+      const float dUdl = kBT_p * (__fdividef(0.25f, (1.0f - x) * (1.0f - x)) - 0.25f + x) - kp * rL2;
+      const float3 fs = (dUdl * rl) * ev;  // F_a = (dU/dl)/l (b - a), F_b = -F_a
       if (k_b == 0.f) {
         add(E.x, fs);
         add(E.y, (-1.0f) * fs);
@@ -198,10 +202,10 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       // sin(theta - theta0) = sin(theta) cos(theta0) - cos(theta) sin(theta0), with
       // cos(theta), sin(theta) from the normals (no inverse trigonometry)
       const float inv = rsqrtf(dot(n1, n1) * dot(n2, n2));
-      const float cth = dot(n1, n2) * inv, sth = dot(cross(n1, n2), ev) / l * inv;
+      const float cth = dot(n1, n2) * inv, sth = dot(cross(n1, n2), ev) * rl * inv;
       const float sb = k_b * (sth * rest.y - cth * rest.z);
-      const float3 gc = (-l / dot(n1, n1)) * n1, gd = (-l / dot(n2, n2)) * n2;
-      const float t1 = dot(dv(E.z, E.x), ev) / L2, t2 = dot(dv(E.w, E.x), ev) / L2;
+      const float3 gc = __fdividef(-l, dot(n1, n1)) * n1, gd = __fdividef(-l, dot(n2, n2)) * n2;
+      const float t1 = dot(dv(E.z, E.x), ev) * rL2, t2 = dot(dv(E.w, E.x), ev) * rL2;
       add(E.x, fs + (sb * (1.0f - t1)) * gc + (sb * (1.0f - t2)) * gd);
       add(E.y, (-1.0f) * fs + (sb * t1) * gc + (sb * t2) * gd);
       add(E.z, (-sb) * gc);
@@ -223,8 +227,8 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       const int vv[3] = {Tr.x, Tr.y, Tr.z};
       const float3 N = normal(t);
       const float At = sA[t];
-      const float coef = k_l * (At - At0) / At0 + cg;
-      const float3 nh = (1.0f / (2.0f * At)) * N;
+      const float coef = k_l * __fdividef(At - At0, At0) + cg;
+      const float3 nh = __fdividef(0.5f, At) * N;
       const float3 fV = (-cv / 6.0f) * N;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {

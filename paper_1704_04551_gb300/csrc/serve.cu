@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(MEMBRANE_THREADS, 4) k_membranes_b(const CaseD
 }
 
 __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_spread_b(const CaseDev* cases, const Item* items) {
-  extern __shared__ __align__(16) int ibox[];
+  extern __shared__ __align__(16) unsigned char ibox[];
   const Item it = items[blockIdx.x];
   const CaseDev& C = cases[it.c];
   if (!C.active) return;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_spread_b(const CaseDe
 }
 
 __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_interpolate_b(const CaseDev* cases, const Item* items) {
-  extern __shared__ __align__(16) float4 fbox[];
+  extern __shared__ __align__(16) unsigned char fbox[];
   const Item it = items[blockIdx.x];
   const CaseDev& C = cases[it.c];
   if (!C.active) return;

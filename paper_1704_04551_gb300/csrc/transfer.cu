@@ -19,15 +19,15 @@ __global__ void k_stencil_cache(MarkersDev m) {
 template <int GEOM>
 __global__ void __launch_bounds__(XFER_THREADS, 2) k_spread(LatticeDev L, MarkersDev m, const MarkerGroup* groups,
                                                             int4* boxes) {
-  extern __shared__ __align__(16) int ibox[];  // [3][vol] fixed-point sums
-  spread_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, ibox);
+  extern __shared__ __align__(16) unsigned char smem[];  // fixed-point box, marker records
+  spread_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, smem);
 }
 
 template <int GEOM>
 __global__ void __launch_bounds__(XFER_THREADS, 2) k_interpolate(LatticeDev L, MarkersDev m,
                                                                  const MarkerGroup* groups, const int4* boxes) {
-  extern __shared__ __align__(16) float4 vbox[];  // [vol] velocities
-  interpolate_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, vbox);
+  extern __shared__ __align__(16) unsigned char smem[];  // velocity box, marker records
+  interpolate_group<GEOM>(L, m, groups[blockIdx.x], boxes + 2 * blockIdx.x, smem);
 }
 
 cudaError_t transfer_configure() {

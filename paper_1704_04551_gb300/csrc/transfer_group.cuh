@@ -21,7 +21,9 @@
 //
 // One thread block per marker group (a body, or a run of tracers), one
 // thread per marker: a thread computes its marker's 12 weights once and
-// visits the 64 stencil nodes itself. The block bounds the group's stencils
+// visits the 64 stencil nodes itself; which marker a lane takes is chosen
+// so that a warp's shared-memory accesses fall in distinct banks (see
+// Residues below). The block bounds the group's stencils
 // with a box; when the box fits in shared memory (BOX_CELLS cells):
 //   spreading accumulates there in 32-bit fixed point (native integer
 //   shared-memory atomics; the sum does not depend on the order of the
@@ -29,8 +31,10 @@
 //   cell can overflow, then adds the box's nonzero cells to global memory
 //   (one float4 atomic each);
 //   interpolation loads the box of velocities (float4 per cell, so that one
-//   16-byte shared load serves a node) once and gathers from shared memory;
-//   the same sweep clears the force density the collision has consumed.
+//   16-byte shared load serves a node) once, with asynchronous copies that
+//   stay in flight while the block sorts its markers, and gathers from
+//   shared memory; the same sweep clears the force density the collision
+//   has consumed.
 // Larger boxes (scattered tracers, very large bodies) fall back to
 // per-marker global float4 atomics / gathers. The box of each group is
 // computed by the spread kernel and reused by the interpolation of the same
@@ -45,10 +49,16 @@ namespace ibm {
 
 namespace xfer_detail {
 
-constexpr int XFER_THREADS = 352;   // 11 warps: a 642-vertex body is two passes at 91 % of the lanes
+constexpr int XFER_THREADS = 352;   // 11 warps
 constexpr int BOX_CELLS = 6144;     // shared-memory box limit (cells)
-constexpr int SPREAD_SMEM = 3 * BOX_CELLS * (int)sizeof(int);     // fixed-point sums, [3][vol]
-constexpr int INTERP_SMEM = BOX_CELLS * (int)sizeof(float4);      // velocities, [vol] float4
+constexpr int XFER_GROUP_MAX = 1024;  // markers per group (records in shared memory)
+constexpr int XFER_PER_THREAD = (XFER_GROUP_MAX + XFER_THREADS - 1) / XFER_THREADS;
+constexpr int RESIDUE_BYTES = 512;   // the counting sort's counters (struct Residues)
+// fixed-point sums [3][vol], two float4 records per marker, counters
+constexpr int SPREAD_SMEM =
+    3 * BOX_CELLS * (int)sizeof(int) + 2 * XFER_GROUP_MAX * (int)sizeof(float4) + RESIDUE_BYTES;
+// velocities [vol] float4, one float4 record per marker, counters
+constexpr int INTERP_SMEM = BOX_CELLS * (int)sizeof(float4) + XFER_GROUP_MAX * (int)sizeof(float4) + RESIDUE_BYTES;
 
 // The four delta weights of one axis for a marker at fractional offset f.
 __device__ __forceinline__ void axis_weights(float f, float w[4]) {
@@ -265,6 +275,45 @@ __device__ __forceinline__ int box_x(int xw0, int ax, int nx) {
   return (ax < nx) ? x - nx : wrapi(x, nx);
 }
 
+// Index in the box of a marker's first stencil node, or -1 if its 4^3
+// stencil is not inside the box.
+__device__ __forceinline__ int box_index(const MarkersDev& m, int k, int4 lo, int4 dims) {
+  const size_t M = (size_t)m.M;
+  const int ox = m.cell[k] - 1 - lo.x, oy = m.cell[M + k] - 1 - lo.y, oz = m.cell[2 * M + k] - 1 - lo.z;
+  if (ox < 0 || oy < 0 || oz < 0 || ox + 4 > dims.x || oy + 4 > dims.y || oz + 4 > dims.z) return -1;
+  return ox + dims.x * (oy + dims.y * oz);
+}
+
+// Lane assignment without shared-memory bank conflicts. Every shared access
+// of a marker's stencil is at box index li0 + (a fixed offset per node), so
+// 32 markers whose li0 differ modulo 32 hit 32 distinct banks with 4-byte
+// accesses (the spreading atomics) and, 8 by 8, distinct bank quads with
+// 16-byte ones (the velocity gather). The group's markers are counted by
+// li0 mod 32 (a counting sort in shared memory); lane r of a warp then takes
+// the w-th marker of residue r. A marker's lane does not change any sum: the
+// fixed-point atomics are order-independent and each gather is one thread's.
+struct Residues {
+  int cnt[32], start[32], cur[32];
+  int most;
+};
+static_assert(sizeof(Residues) <= RESIDUE_BYTES, "counters");
+// after the counts: exclusive prefix (start, cursor) and the largest class
+__device__ __forceinline__ void residue_scan(Residues& R) {
+  if (threadIdx.x < 32) {
+    const int c = R.cnt[threadIdx.x];
+    int incl = c, mx = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)threadIdx.x >= o) incl += v;
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    R.start[threadIdx.x] = incl - c;
+    R.cur[threadIdx.x] = incl - c;
+    if (threadIdx.x == 0) R.most = mx;
+  }
+}
+
 }  // namespace xfer_detail
 using namespace xfer_detail;
 
@@ -295,10 +344,10 @@ __device__ __noinline__ void scatter_global(const LatticeDev& L, const Stencil& 
 
 // Spreading of one marker group by the whole thread block; box_out receives
 // the group's stencil box (origin, size) for the interpolation of this step.
-// ibox: [3][BOX_CELLS] ints of shared memory.
+// smem: SPREAD_SMEM bytes (fixed-point box, then the marker records).
 template <int GEOM>
 __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
-                                             int4* box_out, int* ibox) {
+                                             int4* box_out, unsigned char* smem) {
   int4 lo, dims;
   float fmax;
   group_box(m, G, lo, dims, fmax);  // synchronises
@@ -308,56 +357,89 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   }
   const bool any_force = fmax > 0.f;
   const bool in_smem = dims.w != 0;
-  // touched tiles: from the box when it fits, else marker by marker below
-  if (in_smem) mark_box_tiles<GEOM>(L, lo, dims);
-  if (in_smem && !any_force) return;
+  if (!in_smem) {
+    // per-marker global atomics; touched tiles marker by marker (whole warps
+    // iterate together: shuffles in mark_tiles)
+    for (int j0 = 0; j0 < G.count; j0 += blockDim.x) {
+      if (j0 + (int)(threadIdx.x & ~31u) >= G.count) break;
+      const int j = j0 + threadIdx.x;
+      const bool active = j < G.count;
+      const int k = G.first + (active ? j : 0);
+      Stencil s;
+      load_stencil(m, k, s);
+      mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active);
+      if (active && any_force) scatter_global<GEOM>(L, s, m.F[k]);
+    }
+    return;
+  }
+  mark_box_tiles<GEOM>(L, lo, dims);  // touched tiles: every tile the box meets
+  if (!any_force) return;
+  int* ibox = reinterpret_cast<int*>(smem);                                   // [3][vol]
+  float4* rec = reinterpret_cast<float4*>(smem + 3 * BOX_CELLS * sizeof(int));  // [2][XFER_GROUP_MAX]
+  Residues& R = *reinterpret_cast<Residues*>(rec + 2 * XFER_GROUP_MAX);
   const int vol = dims.x * dims.y * dims.z;
+  const size_t M = (size_t)m.M;
   // Fixed-point scale: a contribution is at most fmax / 8 (delta <= 1/8) and
   // a cell's sum at most count * fmax / 8; S keeps contributions below 2^22
   // (converted exactly by fixed_mul) and sums below 2^30.
-  const float S = any_force ? fminf(33554432.0f, 8589934592.0f / (float)G.count) / fmax : 0.f;
-  if (in_smem) {
-    for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
-    __syncthreads();
+  const float S = fminf(33554432.0f, 8589934592.0f / (float)G.count) / fmax;
+  for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
+  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
+  __syncthreads();
+  // markers by residue of their first node's box index
+  int li[XFER_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    li[q] = j < G.count ? box_index(m, G.first + j, lo, dims) : -1;  // inside by construction of the box
+    if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
   }
-  // one thread per marker; whole warps iterate together (shuffles in mark_tiles)
-  for (int j0 = 0; j0 < G.count; j0 += blockDim.x) {
-    if (j0 + (int)(threadIdx.x & ~31u) >= G.count) break;  // the whole warp is past the group's end
-    const int j = j0 + threadIdx.x;
-    const bool active = j < G.count;
-    const int k = G.first + (active ? j : 0);
-    Stencil s;
-    load_stencil(m, k, s);
-    if (!in_smem) mark_tiles<GEOM>(L, s.bx, s.by, s.bz, active);
-    if (!active || !any_force) continue;
+  __syncthreads();
+  residue_scan(R);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    if (li[q] < 0) continue;
+    const int k = G.first + threadIdx.x + q * XFER_THREADS;
+    const int pos = atomicAdd(&R.cur[li[q] & 31], 1);
     const float4 F = m.F[k];
-    if (in_smem) {
+    rec[pos] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
+    rec[XFER_GROUP_MAX + pos] = make_float4(F.x * S, F.y * S, F.z * S, 0.f);
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int n = R.cnt[lane], st = R.start[lane];
+    for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
+      if (w >= n) continue;
+      const float4 A = rec[st + w], B = rec[XFER_GROUP_MAX + st + w];
+      float wx[4], wy[4], wz[4];
+      axis_weights(A.y, wx);
+      axis_weights(A.z, wy);
+      axis_weights(A.w, wz);
       float fx[4], fy[4], fz[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        fx[a] = F.x * S * s.wx[a];
-        fy[a] = F.y * S * s.wx[a];
-        fz[a] = F.z * S * s.wx[a];
+        fx[a] = B.x * wx[a];
+        fy[a] = B.y * wx[a];
+        fz[a] = B.z * wx[a];
       }
-      const int li0 = (s.bx - lo.x) + dims.x * ((s.by - lo.y) + dims.y * (s.bz - lo.z));
+      const int li0 = __float_as_int(A.x);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          const float w = s.wy[b] * s.wz[c];
+          const float wyz = wy[b] * wz[c];
           int* p = ibox + li0 + dims.x * (b + dims.y * c);
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            atomicAdd(p + a, fixed_mul(fx[a], w));
-            atomicAdd(p + vol + a, fixed_mul(fy[a], w));
-            atomicAdd(p + 2 * vol + a, fixed_mul(fz[a], w));
+            atomicAdd(p + a, fixed_mul(fx[a], wyz));
+            atomicAdd(p + vol + a, fixed_mul(fy[a], wyz));
+            atomicAdd(p + 2 * vol + a, fixed_mul(fz[a], wyz));
           }
         }
-    } else {
-      scatter_global<GEOM>(L, s, F);
     }
   }
-  if (!in_smem) return;
   __syncthreads();
   // add the nonzero cells of the box to the lattice, row by row
   const float inv = 1.0f / S;
@@ -369,8 +451,8 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
     const int x = box_x(xw0, ax, L.nx);
     for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += nwarps * sw.rpw) {
-      const int li = r * dims.x + ax;
-      const int qx = ibox[li], qy = ibox[vol + li], qz = ibox[2 * vol + li];
+      const int i = r * dims.x + ax;
+      const int qx = ibox[i], qy = ibox[vol + i], qz = ibox[2 * vol + i];
       if ((qx | qy | qz) == 0) continue;
       int iy, iz;
       row_yz(r, dims.y, inv_dy, iy, iz);
@@ -417,20 +499,46 @@ __device__ __noinline__ float3 gather_global(const LatticeDev& L, const Stencil&
   return make_float3(ux, uy, uz);
 }
 
+// Advection of marker k by U (FP64) and the stencil cache of the new position.
+__device__ __forceinline__ void advect_marker(const MarkersDev& m, int k, float ux, float uy, float uz) {
+  const size_t M = (size_t)m.M;
+  const float ua[3] = {ux, uy, uz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double Xn = m.X[a * M + k] + (double)ua[a];
+    m.X[a * M + k] = Xn;
+    cache_coord(m, a * M + k, Xn);
+  }
+}
+
 // Interpolation and advection of one marker group by the whole thread block.
-// vbox: [BOX_CELLS] float4 of shared memory.
+// smem: INTERP_SMEM bytes (velocity box, then the marker records).
 template <int GEOM>
 __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
-                                                  const int4* box_in, float4* vbox) {
+                                                  const int4* box_in, unsigned char* smem) {
   const int4 lo = box_in[0], dims = box_in[1];
   const size_t M = (size_t)m.M;
-  const bool in_smem = dims.w != 0;
   const bool moves = !(G.flags & GROUP_FIXED);
-  if (in_smem) {
-    // load the box of velocities row by row (solid rows read as zero) and
-    // clear the force density there, four rows in flight per lane (the
-    // loads are latency-bound: the rows are short)
-    constexpr int RIF = 4;
+  if (dims.w == 0) {
+    // no box: every marker gathers from the lattice and clears what it visits
+    for (int j = threadIdx.x; j < G.count; j += blockDim.x) {
+      const int k = G.first + j;
+      Stencil s;
+      load_stencil(m, k, s);
+      const float3 u = gather_global<GEOM>(L, s, true);
+      m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
+      if (moves) advect_marker(m, k, u.x, u.y, u.z);
+    }
+    return;
+  }
+  float4* vbox = reinterpret_cast<float4*>(smem);               // [vol]
+  float4* rec = vbox + BOX_CELLS;                                // [XFER_GROUP_MAX]
+  Residues& R = *reinterpret_cast<Residues*>(rec + XFER_GROUP_MAX);
+  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
+  {
+    // the box of velocities row by row with asynchronous 16-byte copies
+    // (solid rows are written as zero); the force density there is cleared
+    // (consumed by this step's collision)
     const int nrows = dims.y * dims.z;
     const int nwarps = blockDim.x >> 5;
     const RowSweep sw = row_sweep(dims.x);
@@ -439,71 +547,95 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     const int xw0 = wrapi(lo.x, L.nx);
     for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
       const int x = box_x(xw0, ax, L.nx);
-      for (int r0 = (threadIdx.x >> 5) * sw.rpw + sw.sub; r0 < nrows; r0 += RIF * rstep) {
-        float4 u[RIF];
-#pragma unroll
-        for (int q = 0; q < RIF; ++q) {
-          const int r = r0 + q * rstep;
-          u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          int iy, iz;
-          row_yz(r, dims.y, inv_dy, iy, iz);
-          int y = lo.y + iy, z = lo.z + iz;
-          if (r < nrows && fluid_row<GEOM>(L, y, z)) {
-            const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
-            u[q] = L.uw[gi];
-            L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed by this step's collision
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < RIF; ++q) {
-          const int r = r0 + q * rstep;
-          if (r < nrows) vbox[r * dims.x + ax] = u[q];
+      for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += rstep) {
+        int iy, iz;
+        row_yz(r, dims.y, inv_dy, iy, iz);
+        int y = lo.y + iy, z = lo.z + iz;
+        float4* dst = vbox + r * dims.x + ax;
+        if (fluid_row<GEOM>(L, y, z)) {
+          const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(L.uw + gi) : "memory");
+          L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          *dst = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  for (int j = threadIdx.x; j < G.count; j += blockDim.x) {
-    const int k = G.first + j;
-    Stencil s;
-    load_stencil(m, k, s);
-    float ux = 0.f, uy = 0.f, uz = 0.f;
-    const int ox = s.bx - lo.x, oy = s.by - lo.y, oz = s.bz - lo.z;
-    const bool inside = in_smem && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y &&
-                        oz + 4 <= dims.z;
-    if (inside) {
-      const int li0 = ox + dims.x * (oy + dims.y * oz);
+  __syncthreads();
+  // markers by residue of their first node's box index (-1: outside the box)
+  int li[XFER_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    li[q] = j < G.count ? box_index(m, G.first + j, lo, dims) : -1;
+    if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
+  }
+  __syncthreads();
+  residue_scan(R);
+  __syncthreads();
+  int pos[XFER_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    pos[q] = -1;
+    if (li[q] < 0) continue;
+    const int k = G.first + threadIdx.x + q * XFER_THREADS;
+    pos[q] = atomicAdd(&R.cur[li[q] & 31], 1);
+    rec[pos[q]] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  {
+    // gather: lane r takes the w-th marker of residue r; the result replaces
+    // the marker's record
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int n = R.cnt[lane], st = R.start[lane];
+    for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
+      if (w >= n) continue;
+      const float4 A = rec[st + w];
+      float wx[4], wy[4], wz[4];
+      axis_weights(A.y, wx);
+      axis_weights(A.z, wy);
+      axis_weights(A.w, wz);
+      const int li0 = __float_as_int(A.x);
+      float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
           const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
-          const float rx = fmaf(s.wx[3], v3.x, fmaf(s.wx[2], v2.x, fmaf(s.wx[1], v1.x, s.wx[0] * v0.x)));
-          const float ry = fmaf(s.wx[3], v3.y, fmaf(s.wx[2], v2.y, fmaf(s.wx[1], v1.y, s.wx[0] * v0.y)));
-          const float rz = fmaf(s.wx[3], v3.z, fmaf(s.wx[2], v2.z, fmaf(s.wx[1], v1.z, s.wx[0] * v0.z)));
-          const float w = s.wy[b] * s.wz[c];
-          ux = fmaf(w, rx, ux);
-          uy = fmaf(w, ry, uy);
-          uz = fmaf(w, rz, uz);
+          const float rx = fmaf(wx[3], v3.x, fmaf(wx[2], v2.x, fmaf(wx[1], v1.x, wx[0] * v0.x)));
+          const float ry = fmaf(wx[3], v3.y, fmaf(wx[2], v2.y, fmaf(wx[1], v1.y, wx[0] * v0.y)));
+          const float rz = fmaf(wx[3], v3.z, fmaf(wx[2], v2.z, fmaf(wx[1], v1.z, wx[0] * v0.z)));
+          const float wyz = wy[b] * wz[c];
+          ux = fmaf(wyz, rx, ux);
+          uy = fmaf(wyz, ry, uy);
+          uz = fmaf(wyz, rz, uz);
         }
-    } else {
-      const float3 u = gather_global<GEOM>(L, s, !in_smem);
-      ux = u.x;
-      uy = u.y;
-      uz = u.z;
+      rec[st + w] = make_float4(ux, uy, uz, 0.f);
     }
-    m.U[k] = make_float4(ux, uy, uz, 0.f);
-    if (moves) {
-      // advection (FP64), then the stencil cache of the new position
-      const float ua[3] = {ux, uy, uz};
+  }
+  __syncthreads();
+  // results back in marker order: velocity, advection (FP64), stencil cache
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double Xn = m.X[a * M + k] + (double)ua[a];
-        m.X[a * M + k] = Xn;
-        cache_coord(m, a * M + k, Xn);
-      }
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    if (j >= G.count) continue;
+    const int k = G.first + j;
+    float3 u;
+    if (pos[q] >= 0) {
+      const float4 r = rec[pos[q]];
+      u = make_float3(r.x, r.y, r.z);
+    } else {  // stencil outside the box
+      Stencil s;
+      load_stencil(m, k, s);
+      u = gather_global<GEOM>(L, s, false);
     }
+    m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
+    if (moves) advect_marker(m, k, u.x, u.y, u.z);
   }
 }
 
