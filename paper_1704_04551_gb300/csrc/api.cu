@@ -135,6 +135,10 @@ void drop_graphs(ibm_lbm_t* h) {
       if (g) cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto& g : h->g_fused) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
 }
 
 int tiles(const LatticeDev& L) { return L.ntx * L.nty * L.ntz; }
@@ -210,6 +214,49 @@ int capture(ibm_lbm_t* h, cudaGraphExec_t* out, int n, bool odd0, bool dense_las
   return IBM_LBM_OK;
 }
 
+// The fused path: n (even) coupled steps starting at an even AA step. The
+// first step's forces and spreading run as separate kernels into the first
+// force-density buffer; then every step is the collision (reading the
+// buffer of its parity) followed by the fused kernel, which interpolates and
+// advects, computes the forces at the new positions and spreads them into
+// the other buffer; the last step's interpolation runs alone. The tile flags
+// are cleared between a collision and the spreading that follows it.
+bool fused_applies(const ibm_lbm_t* h) {
+  return h->n_couple > 0 && !h->timing && !(h->morse_rc > 0.0) && h->gbuf2 != nullptr;
+}
+
+void enqueue_fused_chunk(ibm_lbm_t* h, int n) {
+  cudaStream_t st = h->stream;
+  LatticeDev L0 = h->L;
+  L0.g = h->gbuf;
+  cudaMemsetAsync(L0.flags, 0, (size_t)tiles(L0), st);
+  enqueue_forces(h, st);
+  launch_spread(L0, h->m, h->groups, h->n_groups, h->boxes, st);
+  for (int s = 0; s < n; ++s) {
+    LatticeDev Ls = h->L;
+    Ls.g = (s & 1) ? h->gbuf2 : h->gbuf;
+    launch_collide(Ls, h->rows, h->n_rows, h->cfg.storage, (s & 1) != 0, false, st);
+    if (s + 1 < n) {
+      cudaMemsetAsync(Ls.flags, 0, (size_t)tiles(Ls), st);
+      launch_couple(Ls, (s & 1) ? h->gbuf : h->gbuf2, h->m, h->d_bodies, h->couple_items, h->n_couple, h->groups,
+                    h->boxes, h->mesh, st);
+    } else {
+      launch_interpolate(Ls, h->m, h->groups, h->n_groups, h->boxes, st);
+    }
+  }
+}
+
+int capture_fused(ibm_lbm_t* h, cudaGraphExec_t* out, int n) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_fused_chunk(h, n);
+  CUDA_TRY(h, cudaStreamEndCapture(h->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, IBM_LBM_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return IBM_LBM_OK;
+}
+
 int enqueue_diagnostics(ibm_lbm_t* h) {
   cudaStream_t st = h->stream;
   CUDA_TRY(h, cudaMemsetAsync(h->d_diag, 0, 8 * sizeof(double), st));
@@ -252,8 +299,23 @@ int enqueue_steps(ibm_lbm_t* h, int64_t n) {
     CUDA_TRY(h, cudaGetLastError());
     return enqueue_diagnostics(h);
   }
+  if (h->n_couple > 0 && !h->gbuf2 && !h->timing && left > CHUNK) {
+    // second force-density buffer of the fused path, zero like the first
+    h->gbuf2 = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * (size_t)h->L.N);
+    if (h->gbuf2) CUDA_TRY(h, cudaMemsetAsync(h->gbuf2, 0, sizeof(float4) * (size_t)h->L.N, h->stream));
+  }
   while (left > 0) {
-    if (!h->odd_next && left > CHUNK) {
+    if (fused_applies(h) && !h->odd_next && left > CHUNK) {
+      const int which = left > FUSED_LONG ? 0 : 1;
+      const int n = which == 0 ? FUSED_LONG : CHUNK;
+      if (!h->g_fused[which]) {
+        int rc = capture_fused(h, &h->g_fused[which], n);
+        if (rc) return rc;
+      }
+      CUDA_TRY(h, cudaGraphLaunch(h->g_fused[which], h->stream));
+      left -= n;
+      h->steps += n;
+    } else if (!h->odd_next && left > CHUNK) {
       if (!h->g_chunk) {
         int rc = capture(h, &h->g_chunk, CHUNK, false, false);
         if (rc) return rc;
@@ -579,7 +641,7 @@ static int impl_ibm_lbm_create(const ibm_lbm_config* cfg, const ibm_lbm_allocato
   }
   if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
     return bail(IBM_LBM_E_CUDA);
-  if (transfer_configure() != cudaSuccess) {
+  if (transfer_configure() != cudaSuccess || couple_configure() != cudaSuccess) {
     cudaGetLastError();
     return bail(IBM_LBM_E_CUDA);
   }
@@ -706,6 +768,8 @@ static void clear_markers(ibm_lbm_t* h) {
   h->groups = nullptr;
   h->n_groups = 0;
   h->boxes = nullptr;
+  h->couple_items = nullptr;
+  h->n_couple = 0;
   h->need_zero_F = false;
 }
 
@@ -929,6 +993,24 @@ static int set_markers_into(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bo
     }
     h->n_groups = (int)groups.size();
     if ((rc = upload<MarkerGroup>(h, h->marker_mem, &h->groups, groups.data(), groups.size()))) return rc;
+    // fused path: every marker belongs to a membrane whose template fits the
+    // fused kernel, one transfer group per body
+    bool fused = n_bodies > 0 && covered == n_markers && any_membrane && couple_fits(h->mesh);
+    for (int b = 0; b < n_bodies && fused; ++b) fused = bodies[b].kind == IBM_LBM_BODY_MEMBRANE;
+    if (fused) {
+      std::unordered_map<int, int> body_of_first;
+      for (int b = 0; b < n_bodies; ++b) body_of_first[(int)bodies[b].first] = b;
+      std::vector<int2> items;
+      for (size_t g = 0; g < groups.size() && fused; ++g) {
+        auto it = body_of_first.find(groups[g].first);
+        if (it == body_of_first.end() || groups[g].count != (int)bodies[it->second].count) fused = false;
+        else items.push_back(make_int2(it->second, (int)g));
+      }
+      if (fused && (int)items.size() == n_bodies) {
+        if ((rc = upload<int2>(h, h->marker_mem, &h->couple_items, items.data(), items.size()))) return rc;
+        h->n_couple = (int)items.size();
+      }
+    }
     h->boxes = (int4*)dalloc(h, h->marker_mem, sizeof(int4) * 2 * std::max<size_t>(1, groups.size()));
     if (!h->boxes) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
     // no box until the first spreading: an interpolation run before it (the

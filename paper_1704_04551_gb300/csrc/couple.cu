@@ -1,0 +1,304 @@
+// Fused coupling kernel for suspensions of membranes: one thread block per
+// membrane body does, between the collision of step n and that of step n+1,
+//   1. the interpolation of step n (Eq. ibmVelocityInterpret) from the box of
+//      velocities the collision wrote, and the advection X^{n+1} = X^n + U
+//      (FP64), clearing the force density the collision consumed;
+//   2. the membrane forces at X^{n+1} (Sec. 2.2, Eqs. membrane-potential ..
+//      volumeEnergy), from the new positions kept in shared memory;
+//   3. the spreading of those forces for step n+1 (Eq. ibmForceSpread) into
+//      the other force-density buffer, and the touched tiles of step n+1.
+// The arithmetic of each part is that of the separate kernels (the device
+// bodies are shared: transfer_group.cuh, forces_body.cuh); what the fusion
+// removes is two kernel boundaries, the reloading of the stencil cache and
+// of the marker forces between the parts, and the bounding-box pass of the
+// spreading. Two force-density buffers are needed: a block clears the one
+// the collision of step n read while other blocks already spread into the
+// one the collision of step n+1 reads.
+//
+// Shared memory (the parts reuse one region): the velocity box and the
+// marker records (part 1); then the vertex positions and forces, the
+// triangle normals and areas (part 2); then the fixed-point box and the
+// marker order (part 3), placed after the positions and forces, which part
+// 3 still reads.
+#include "common.cuh"
+#include "forces_body.cuh"
+#include "internal.h"
+#include "transfer_group.cuh"
+
+namespace ibm {
+
+namespace {
+
+// Stencil of vertex v from the positions in shared memory (integer parts
+// relative to o, fractions).
+__device__ __forceinline__ void smem_cell(const MembraneSmem& S, int nv, int v, int3 o, int c[3], float f[3]) {
+  c[0] = o.x + (int)S.sI[v];
+  c[1] = o.y + (int)S.sI[nv + v];
+  c[2] = o.z + (int)S.sI[2 * nv + v];
+  f[0] = S.sR[v];
+  f[1] = S.sR[nv + v];
+  f[2] = S.sR[2 * nv + v];
+}
+
+template <int GEOM>
+__device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* B,
+                                                const MarkerGroup G, int4* box, const MeshDev& mesh,
+                                                unsigned char* smem, double* red) {
+  __shared__ int s_lo[3], s_hi[3];
+  __shared__ unsigned s_fmax;
+  const size_t M = (size_t)m.M;
+  const int nv = mesh.nv, nt = mesh.nt;  // G.count == nv
+  const int4 lo = box[0], dims = box[1];
+  const bool in_box = dims.w != 0;
+  float4* vbox = reinterpret_cast<float4*>(smem);
+  float4* rec = vbox + BOX_CELLS;                                 // [nv]
+  Residues& R = *reinterpret_cast<Residues*>(rec + nv);
+  // origin of the integer parts in shared memory: the first vertex's cell
+  // before this step's advection (read before any thread writes the cache)
+  const int3 o = make_int3(m.cell[G.first], m.cell[M + G.first], m.cell[2 * M + G.first]);
+
+  // ---- 1. interpolation of step n and advection --------------------------
+  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
+  if (in_box) velocity_box_async<GEOM>(L, lo, dims, vbox);
+  __syncthreads();
+  int li[XFER_PER_THREAD], pos[XFER_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    li[q] = (in_box && j < G.count) ? box_index(m, G.first + j, lo, dims) : -1;
+    if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
+  }
+  __syncthreads();
+  residue_scan(R);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    pos[q] = -1;
+    if (li[q] < 0) continue;
+    const int k = G.first + threadIdx.x + q * XFER_THREADS;
+    pos[q] = atomicAdd(&R.cur[li[q] & 31], 1);
+    rec[pos[q]] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
+  }
+  velocity_box_wait();
+  __syncthreads();
+  gather_records(vbox, dims, R, rec);
+  __syncthreads();
+  const MembraneSmem S = MembraneSmem::at(smem, nv, nt);  // over the velocity box, which is done
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    if (j >= G.count) continue;
+    const int k = G.first + j;
+    float3 u;
+    if (pos[q] >= 0) {
+      const float4 r = rec[pos[q]];
+      u = make_float3(r.x, r.y, r.z);
+    } else {  // no box, or the stencil outside it
+      Stencil st;
+      load_stencil(m, k, st);
+      u = gather_global<GEOM>(L, st, !in_box);
+    }
+    m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
+    const float ua[3] = {u.x, u.y, u.z};
+    const int oa[3] = {o.x, o.y, o.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double Xn = m.X[a * M + k] + (double)ua[a];
+      m.X[a * M + k] = Xn;
+      const double fl = floor(Xn);
+      const int c = (int)fl;
+      const float f = (float)(Xn - fl);
+      m.cell[a * M + k] = c;
+      m.frac[a * M + k] = f;
+      S.sI[a * nv + j] = (float)(c - oa[a]);
+      S.sR[a * nv + j] = f;
+    }
+  }
+  __syncthreads();
+
+  // ---- 2. membrane forces at X^{n+1} ---------------------------------------
+  membrane_core(B, mesh, S, red);  // ends synchronised
+  const float* sF = reinterpret_cast<const float*>(S.sQ);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x)
+    m.F[G.first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+
+  // ---- 3. spreading of step n+1 into g_next -------------------------------
+  // stencil box and largest force component of the new positions
+  if (threadIdx.x < 3) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  if (threadIdx.x == 0) s_fmax = 0u;
+  __syncthreads();
+  {
+    int l[3] = {INT_MAX, INT_MAX, INT_MAX}, h[3] = {INT_MIN, INT_MIN, INT_MIN};
+    float fm = 0.f;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      int c[3];
+      float f[3];
+      smem_cell(S, nv, v, o, c, f);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        l[a] = min(l[a], c[a]);
+        h[a] = max(h[a], c[a]);
+      }
+      fm = fmaxf(fm, fmaxf(fabsf(sF[v]), fmaxf(fabsf(sF[nv + v]), fabsf(sF[2 * nv + v]))));
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        l[a] = min(l[a], __shfl_xor_sync(0xffffffffu, l[a], w));
+        h[a] = max(h[a], __shfl_xor_sync(0xffffffffu, h[a], w));
+      }
+      fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, w));
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&s_lo[a], l[a]);
+        atomicMax(&s_hi[a], h[a]);
+      }
+      atomicMax(&s_fmax, __float_as_uint(fm));  // non-negative floats order as their bits
+    }
+  }
+  __syncthreads();
+  const long long ex = (long long)s_hi[0] - s_lo[0] + 4, ey = (long long)s_hi[1] - s_lo[1] + 4,
+                  ez = (long long)s_hi[2] - s_lo[2] + 4;
+  const int4 lo2 = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, 0);
+  const bool fits = ex > 0 && ey > 0 && ez > 0 && ex * ey * ez <= BOX_CELLS;
+  const int4 dims2 = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
+  const float fmax = __uint_as_float(s_fmax);
+  if (threadIdx.x == 0) {
+    box[0] = lo2;
+    box[1] = dims2;
+  }
+  LatticeDev Ln = L;
+  Ln.g = g_next;
+  if (!fits) {
+    // per-vertex global atomics; touched tiles vertex by vertex (whole warps
+    // iterate together: shuffles in mark_tiles)
+    for (int j0 = 0; j0 < nv; j0 += blockDim.x) {
+      if (j0 + (int)(threadIdx.x & ~31u) >= nv) break;
+      const int v = j0 + threadIdx.x;
+      const bool active = v < nv;
+      const int vv = active ? v : 0;
+      int c[3];
+      float f[3];
+      smem_cell(S, nv, vv, o, c, f);
+      Stencil st;
+      st.bx = c[0] - 1;
+      st.by = c[1] - 1;
+      st.bz = c[2] - 1;
+      axis_weights(f[0], st.wx);
+      axis_weights(f[1], st.wy);
+      axis_weights(f[2], st.wz);
+      mark_tiles<GEOM>(Ln, st.bx, st.by, st.bz, active);
+      if (active && fmax > 0.f)
+        scatter_global<GEOM>(Ln, st, make_float4(sF[vv], sF[nv + vv], sF[2 * nv + vv], 0.f));
+    }
+    return;
+  }
+  mark_box_tiles<GEOM>(Ln, lo2, dims2);
+  if (!(fmax > 0.f)) return;
+  // fixed-point box after the positions and forces (still read below)
+  int* ibox = reinterpret_cast<int*>(S.sQ + 3 * nv);
+  unsigned short* order = reinterpret_cast<unsigned short*>(ibox + 3 * BOX_CELLS);
+  const int vol = dims2.x * dims2.y * dims2.z;
+  const float Sc = fminf(33554432.0f, 8589934592.0f / (float)nv) / fmax;  // as in spread_group
+  for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
+  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int l2[XFER_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+    const int v = threadIdx.x + q * XFER_THREADS;
+    l2[q] = -1;
+    if (v >= nv) continue;
+    int c[3];
+    float f[3];
+    smem_cell(S, nv, v, o, c, f);
+    l2[q] = (c[0] - 1 - lo2.x) + dims2.x * ((c[1] - 1 - lo2.y) + dims2.y * (c[2] - 1 - lo2.z));
+    atomicAdd(&R.cnt[l2[q] & 31], 1);
+  }
+  __syncthreads();
+  residue_scan(R);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < XFER_PER_THREAD; ++q)
+    if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * XFER_THREADS);
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int n = R.cnt[lane], st = R.start[lane];
+    for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
+      if (w >= n) continue;
+      const int v = order[st + w];
+      int c[3];
+      float f[3];
+      smem_cell(S, nv, v, o, c, f);
+      const int li0 = (c[0] - 1 - lo2.x) + dims2.x * ((c[1] - 1 - lo2.y) + dims2.y * (c[2] - 1 - lo2.z));
+      scatter_marker(ibox, vol, dims2, li0, f[0], f[1], f[2], sF[v] * Sc, sF[nv + v] * Sc, sF[2 * nv + v] * Sc);
+    }
+  }
+  __syncthreads();
+  flush_box<GEOM>(Ln, lo2, dims2, ibox, 1.0f / Sc);
+}
+
+template <int GEOM>
+__global__ void __launch_bounds__(XFER_THREADS, 2)
+    k_couple(LatticeDev L, float4* g_next, MarkersDev m, BodyDev* __restrict__ bodies, const int2* __restrict__ items,
+             const MarkerGroup* __restrict__ groups, int4* boxes, MeshDev mesh) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[2 * 32];
+  const int2 it = items[blockIdx.x];  // (body, its transfer group)
+  couple_membrane<GEOM>(L, g_next, m, bodies + it.x, groups[it.y], boxes + 2 * it.y, mesh, smem, red);
+}
+
+}  // namespace
+
+// Shared memory of the fused kernel for a template of nv vertices: the
+// velocity box, one record per vertex, the counters. The forces' region
+// (positions, forces, normals, areas) and the spreading's (positions and
+// forces, fixed-point box, vertex order) must fit below the counters
+// (couple_fits); at 642 vertices the kernel takes 107 KiB, two blocks per SM.
+constexpr int COUPLE_SMEM_MAX = INTERP_SMEM;
+
+size_t couple_smem(const MeshDev& mesh) {
+  return (size_t)BOX_CELLS * sizeof(float4) + (size_t)mesh.nv * sizeof(float4) + RESIDUE_BYTES;
+}
+
+bool couple_fits(const MeshDev& mesh) {
+  const size_t pos_forces = (size_t)9 * mesh.nv * sizeof(float);
+  const size_t normals = (size_t)4 * mesh.nt * sizeof(float);
+  const size_t spread = (size_t)3 * BOX_CELLS * sizeof(int) + (size_t)mesh.nv * sizeof(unsigned short);
+  const size_t below = couple_smem(mesh) - RESIDUE_BYTES;
+  return mesh.nv >= 1 && mesh.nv <= XFER_GROUP_MAX && pos_forces + normals <= below && pos_forces + spread <= below;
+}
+
+cudaError_t couple_configure() {
+  cudaError_t e = cudaSuccess;
+#define CFG(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, COUPLE_SMEM_MAX)
+  CFG(k_couple<GEOM_PERIODIC>); CFG(k_couple<GEOM_YWALLS>); CFG(k_couple<GEOM_TUBE>);
+#undef CFG
+  return e;
+}
+
+void launch_couple(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* bodies, const int2* items,
+                   int n_items, const MarkerGroup* groups, int4* boxes, const MeshDev& mesh, cudaStream_t st) {
+  if (n_items == 0) return;
+  const size_t smem = couple_smem(mesh);
+  switch (L.geometry) {
+    case GEOM_PERIODIC:
+      k_couple<GEOM_PERIODIC><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      break;
+    case GEOM_YWALLS:
+      k_couple<GEOM_YWALLS><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      break;
+    default:
+      k_couple<GEOM_TUBE><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      break;
+  }
+}
+
+}  // namespace ibm

@@ -78,44 +78,78 @@ __device__ __forceinline__ Topo topo_at(const unsigned char* base, const MeshDev
 }  // namespace forces_detail
 using namespace forces_detail;
 
+// Shared-memory views of the membrane force core: vertex positions as
+// integer part (floats, relative to any common origin: exact) and fraction,
+// force sums, triangle normals and areas.
+struct MembraneSmem {
+  float* sI;  // [3][nv]
+  float* sR;  // [3][nv]
+  int* sQ;    // [3][nv] force sums (fixed point, or float bits); on return the forces as floats
+  float* sN;  // [3][nt] doubled-area normals
+  float* sA;  // [nt] areas
+  __device__ static MembraneSmem at(unsigned char* base, int nv, int nt) {
+    MembraneSmem S;
+    S.sI = reinterpret_cast<float*>(base);
+    S.sR = S.sI + 3 * nv;
+    S.sQ = reinterpret_cast<int*>(S.sR + 3 * nv);
+    S.sN = reinterpret_cast<float*>(S.sQ + 3 * nv);
+    S.sA = S.sN + 3 * nt;
+    return S;
+  }
+};
+
+__device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S, double* red);
+
 // Membrane forces of one body by the whole thread block. smem: [9 nv + 4 nt]
 // words (positions as floor + fraction, force sums, normals, areas);
 // red: [2 * 32] doubles.
 //
 // The force sums are scattered with shared-memory integer atomics in fixed
 // point (native and order-independent; float atomics on shared memory are
-// several times slower): each contribution is scaled by S = qcap / (4 q),
+// several times slower): each contribution is scaled by Sq = qcap / (4 q),
 // q the body's largest contribution component of the previous step, so that
 // contributions up to four times larger than last step's fit in qcap units
 // and no vertex sum can overflow. A block that meets a larger contribution,
 // or has no previous step, redoes the scatter with float atomics. The
-// quantum 1/S is ~3e-8 q, below the FP32 rounding of the sums.
+// quantum 1/Sq is ~3e-8 q, below the FP32 rounding of the sums.
 __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp, const MeshDev& mesh,
                                                unsigned char* smem, double* red) {
-  const Topo T = topo_at(mesh.packed, mesh);
   const size_t M = (size_t)m.M;
-  const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
-  const float kBT_p = Bp->kBT_p, k_b = Bp->k_b, k_l = Bp->k_l, k_g = Bp->k_g, k_v = Bp->k_v;
-  const float q_prev = Bp->qmax;
-  float* sI = reinterpret_cast<float*>(smem);         // [3][nv] floor(X) - floor(X_0), exact
-  float* sR = sI + 3 * nv;                            // [3][nv] X - floor(X)
-  int* sQ = reinterpret_cast<int*>(sR + 3 * nv);      // [3][nv] force sums (fixed point, or float bits)
-  float* sN = reinterpret_cast<float*>(sQ + 3 * nv);  // [3][nt] doubled-area normals
-  float* sA = sN + 3 * nt;                            // [nt] areas
-  __shared__ float s_dev[2];
-  __shared__ unsigned s_qmax;
+  const int nv = mesh.nv;
+  const MembraneSmem S = MembraneSmem::at(smem, nv, mesh.nt);
   const int first = Bp->first;
   const int c0[3] = {m.cell[first], m.cell[M + first], m.cell[2 * M + first]};
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      sI[a * nv + v] = (float)(m.cell[a * M + first + v] - c0[a]);
-      sR[a * nv + v] = m.frac[a * M + first + v];
-      sQ[a * nv + v] = 0;
+      S.sI[a * nv + v] = (float)(m.cell[a * M + first + v] - c0[a]);
+      S.sR[a * nv + v] = m.frac[a * M + first + v];
     }
   }
-  if (threadIdx.x == 0) s_qmax = 0u;
   __syncthreads();
+  membrane_core(Bp, mesh, S, red);
+  const float* sF = reinterpret_cast<const float*>(S.sQ);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x)
+    m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+}
+
+// Forces of one membrane whose positions are in S.sI / S.sR (the caller has
+// synchronised after writing them): S.sQ receives the forces as floats
+// [3][nv], Bp->qmax the scale for the next step; ends synchronised.
+__device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S, double* red) {
+  const Topo T = topo_at(mesh.packed, mesh);
+  const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
+  const float kBT_p = Bp->kBT_p, k_b = Bp->k_b, k_l = Bp->k_l, k_g = Bp->k_g, k_v = Bp->k_v;
+  const float q_prev = Bp->qmax;
+  const float* sI = S.sI;
+  const float* sR = S.sR;
+  int* sQ = S.sQ;
+  float* sN = S.sN;
+  float* sA = S.sA;
+  __shared__ float s_dev[2];
+  __shared__ unsigned s_qmax;
+  for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) sQ[i] = 0;
+  if (threadIdx.x == 0) s_qmax = 0u;
   // x_a - x_b, exact in the integer part, one FP32 rounding in the fraction
   auto dv = [&](int a, int b) {
     return make_float3((sI[a] - sI[b]) + (sR[a] - sR[b]), (sI[nv + a] - sI[nv + b]) + (sR[nv + a] - sR[nv + b]),
@@ -238,19 +272,19 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
       }
     }
   };
-  const float S = q_prev > 0.f ? mesh.qcap / (4.0f * q_prev) : 0.f;
+  const float Sq = q_prev > 0.f ? mesh.qcap / (4.0f * q_prev) : 0.f;
   bool over = !(q_prev > 0.f);
   if (!over) {
     pass_b([&](int v, float3 f) {
       const float c = fmaxf(fabsf(f.x), fmaxf(fabsf(f.y), fabsf(f.z)));
       qmax = fmaxf(qmax, c);
-      if (!(c * S <= mesh.qcap)) {  // also catches non-finite values
+      if (!(c * Sq <= mesh.qcap)) {  // also catches non-finite values
         over = true;
         return;
       }
-      atomicAdd(sQ + v, __float2int_rn(f.x * S));
-      atomicAdd(sQ + nv + v, __float2int_rn(f.y * S));
-      atomicAdd(sQ + 2 * nv + v, __float2int_rn(f.z * S));
+      atomicAdd(sQ + v, __float2int_rn(f.x * Sq));
+      atomicAdd(sQ + nv + v, __float2int_rn(f.y * Sq));
+      atomicAdd(sQ + 2 * nv + v, __float2int_rn(f.z * Sq));
     });
   }
   const bool fallback = __syncthreads_or(over) != 0;
@@ -269,19 +303,15 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
   for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
   if ((threadIdx.x & 31) == 0) atomicMax(&s_qmax, __float_as_uint(qmax));  // non-negative floats order as their bits
   __syncthreads();
-  if (fallback) {
-    const float* sF = reinterpret_cast<const float*>(sQ);
-    for (int v = threadIdx.x; v < nv; v += blockDim.x)
-      m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
-  } else {
-    const float inv = 1.0f / S;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x)
-      m.F[first + v] = make_float4((float)sQ[v] * inv, (float)sQ[nv + v] * inv, (float)sQ[2 * nv + v] * inv, 0.f);
+  if (!fallback) {
+    const float inv = 1.0f / Sq;
+    for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) sQ[i] = __float_as_int((float)sQ[i] * inv);
   }
   if (threadIdx.x == 0) {
     const float q = __uint_as_float(s_qmax);
     Bp->qmax = isfinite(q) ? q : 0.f;
   }
+  __syncthreads();
 }
 
 // Filament forces of one bead chain (polymer particles, Sec. 2.2) by the

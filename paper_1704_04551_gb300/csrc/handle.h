@@ -12,6 +12,7 @@
 
 namespace ibm {
 constexpr int CHUNK = 16;          // steps per captured chunk graph (even)
+constexpr int FUSED_LONG = 64;     // steps per long fused chunk graph (even)
 constexpr int MAX_MESH_VERTICES = 4096;
 constexpr int BODY_GROUP = 1024;   // markers per transfer block within a body
 constexpr int TRACER_GROUP = 256;  // markers per transfer block for passive tracers
@@ -63,6 +64,12 @@ struct ibm_lbm {
   MarkerGroup* groups = nullptr;  // transfer blocks
   int n_groups = 0;
   int4* boxes = nullptr;          // per group: stencil box origin and size
+  // Fused coupling (suspensions of membranes only): one block per body
+  // interpolates, computes the forces and spreads; the collision of
+  // alternate steps reads the two force-density buffers in turn.
+  int2* couple_items = nullptr;   // (body, its transfer group) in group order
+  int n_couple = 0;               // > 0: the fused path applies to these markers
+  float4* gbuf2 = nullptr;        // second force density (allocated on first use)
   bool boxes_valid = false;       // boxes match the markers' current positions (stage interface)
   bool need_zero_F = false;
   // state
@@ -81,6 +88,7 @@ struct ibm_lbm {
   bool timing = false;
   // graphs
   cudaGraphExec_t g_chunk = nullptr;
+  cudaGraphExec_t g_fused[2] = {nullptr, nullptr};  // fused chunks of FUSED_LONG and CHUNK steps
   cudaGraphExec_t g_single[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   std::string err;
 };

@@ -34,6 +34,12 @@ size_t membrane_work_floats(int nv, int nt, int ne);
 cudaError_t forces_configure(const MeshDev& mesh, size_t max_smem);
 void launch_filaments(const MarkersDev& m, const BodyDev* bodies, const int* list, int n, cudaStream_t st);
 
+// couple.cu (membrane suspensions: interpolation, forces and spreading fused per body)
+bool couple_fits(const MeshDev& mesh);
+cudaError_t couple_configure();
+void launch_couple(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* bodies, const int2* items,
+                   int n_items, const MarkerGroup* groups, int4* boxes, const MeshDev& mesh, cudaStream_t st);
+
 // solid.cu
 void launch_solid_half(const MarkersDev& m, double* v, const double* fext, double dt, double gamma, double mass,
                        bool first, cudaStream_t st);

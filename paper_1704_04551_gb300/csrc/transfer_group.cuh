@@ -342,6 +342,128 @@ __device__ __noinline__ void scatter_global(const LatticeDev& L, const Stencil& 
   }
 }
 
+// Adds one marker's force, already multiplied by the fixed-point scale, to
+// the box: li0 is the box index of its first stencil node, f its fractional
+// offsets (the weights), vol the box's cells per component.
+__device__ __forceinline__ void scatter_marker(int* ibox, int vol, int4 dims, int li0, float fx, float fy, float fz,
+                                               float Fx, float Fy, float Fz) {
+  float wx[4], wy[4], wz[4];
+  axis_weights(fx, wx);
+  axis_weights(fy, wy);
+  axis_weights(fz, wz);
+  float ax_[4], ay_[4], az_[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ax_[a] = Fx * wx[a];
+    ay_[a] = Fy * wx[a];
+    az_[a] = Fz * wx[a];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float wyz = wy[b] * wz[c];
+      int* p = ibox + li0 + dims.x * (b + dims.y * c);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        atomicAdd(p + a, fixed_mul(ax_[a], wyz));
+        atomicAdd(p + vol + a, fixed_mul(ay_[a], wyz));
+        atomicAdd(p + 2 * vol + a, fixed_mul(az_[a], wyz));
+      }
+    }
+}
+
+// Adds the nonzero cells of a fixed-point box (1/inv units) to L.g, row by
+// row (one float4 atomic per cell).
+template <int GEOM>
+__device__ __forceinline__ void flush_box(const LatticeDev& L, int4 lo, int4 dims, const int* ibox, float inv) {
+  const int vol = dims.x * dims.y * dims.z;
+  const int nrows = dims.y * dims.z;
+  const int nwarps = blockDim.x >> 5;
+  const RowSweep sw = row_sweep(dims.x);
+  const float inv_dy = 1.0f / (float)dims.y;
+  const int xw0 = wrapi(lo.x, L.nx);
+  for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
+    const int x = box_x(xw0, ax, L.nx);
+    for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += nwarps * sw.rpw) {
+      const int i = r * dims.x + ax;
+      const int qx = ibox[i], qy = ibox[vol + i], qz = ibox[2 * vol + i];
+      if ((qx | qy | qz) == 0) continue;
+      int iy, iz;
+      row_yz(r, dims.y, inv_dy, iy, iz);
+      int y = lo.y + iy, z = lo.z + iz;
+      if (!fluid_row<GEOM>(L, y, z)) continue;
+      atomicAdd(L.g + (size_t)L.nx * (y + L.ny * z) + x,
+                make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
+    }
+  }
+}
+
+// Issues the load of the box of velocities (row by row, asynchronous 16-byte
+// copies; solid rows are written as zero) and clears the force density
+// there (consumed by this step's collision). The copies complete at
+// velocity_box_wait() followed by a barrier.
+template <int GEOM>
+__device__ __forceinline__ void velocity_box_async(const LatticeDev& L, int4 lo, int4 dims, float4* vbox) {
+  const int nrows = dims.y * dims.z;
+  const int nwarps = blockDim.x >> 5;
+  const RowSweep sw = row_sweep(dims.x);
+  const int rstep = nwarps * sw.rpw;
+  const float inv_dy = 1.0f / (float)dims.y;
+  const int xw0 = wrapi(lo.x, L.nx);
+  for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
+    const int x = box_x(xw0, ax, L.nx);
+    for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += rstep) {
+      int iy, iz;
+      row_yz(r, dims.y, inv_dy, iy, iz);
+      int y = lo.y + iy, z = lo.z + iz;
+      float4* dst = vbox + r * dims.x + ax;
+      if (fluid_row<GEOM>(L, y, z)) {
+        const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(L.uw + gi) : "memory");
+        L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void velocity_box_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Velocity at every marker of the records (li0, fractional offsets): lane r
+// takes the w-th marker of residue r; each result (u, 0) replaces its record.
+__device__ __forceinline__ void gather_records(const float4* vbox, int4 dims, const Residues& R, float4* rec) {
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int n = R.cnt[lane], st = R.start[lane];
+  for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
+    if (w >= n) continue;
+    const float4 A = rec[st + w];
+    float wx[4], wy[4], wz[4];
+    axis_weights(A.y, wx);
+    axis_weights(A.z, wy);
+    axis_weights(A.w, wz);
+    const int li0 = __float_as_int(A.x);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
+        const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
+        const float rx = fmaf(wx[3], v3.x, fmaf(wx[2], v2.x, fmaf(wx[1], v1.x, wx[0] * v0.x)));
+        const float ry = fmaf(wx[3], v3.y, fmaf(wx[2], v2.y, fmaf(wx[1], v1.y, wx[0] * v0.y)));
+        const float rz = fmaf(wx[3], v3.z, fmaf(wx[2], v2.z, fmaf(wx[1], v1.z, wx[0] * v0.z)));
+        const float wyz = wy[b] * wz[c];
+        ux = fmaf(wyz, rx, ux);
+        uy = fmaf(wyz, ry, uy);
+        uz = fmaf(wyz, rz, uz);
+      }
+    rec[st + w] = make_float4(ux, uy, uz, 0.f);
+  }
+}
+
 // Spreading of one marker group by the whole thread block; box_out receives
 // the group's stencil box (origin, size) for the interpolation of this step.
 // smem: SPREAD_SMEM bytes (fixed-point box, then the marker records).
@@ -413,55 +535,11 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
     for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
       if (w >= n) continue;
       const float4 A = rec[st + w], B = rec[XFER_GROUP_MAX + st + w];
-      float wx[4], wy[4], wz[4];
-      axis_weights(A.y, wx);
-      axis_weights(A.z, wy);
-      axis_weights(A.w, wz);
-      float fx[4], fy[4], fz[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        fx[a] = B.x * wx[a];
-        fy[a] = B.y * wx[a];
-        fz[a] = B.z * wx[a];
-      }
-      const int li0 = __float_as_int(A.x);
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float wyz = wy[b] * wz[c];
-          int* p = ibox + li0 + dims.x * (b + dims.y * c);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            atomicAdd(p + a, fixed_mul(fx[a], wyz));
-            atomicAdd(p + vol + a, fixed_mul(fy[a], wyz));
-            atomicAdd(p + 2 * vol + a, fixed_mul(fz[a], wyz));
-          }
-        }
+      scatter_marker(ibox, vol, dims, __float_as_int(A.x), A.y, A.z, A.w, B.x, B.y, B.z);
     }
   }
   __syncthreads();
-  // add the nonzero cells of the box to the lattice, row by row
-  const float inv = 1.0f / S;
-  const int nrows = dims.y * dims.z;
-  const int nwarps = blockDim.x >> 5;
-  const RowSweep sw = row_sweep(dims.x);
-  const float inv_dy = 1.0f / (float)dims.y;
-  const int xw0 = wrapi(lo.x, L.nx);
-  for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
-    const int x = box_x(xw0, ax, L.nx);
-    for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += nwarps * sw.rpw) {
-      const int i = r * dims.x + ax;
-      const int qx = ibox[i], qy = ibox[vol + i], qz = ibox[2 * vol + i];
-      if ((qx | qy | qz) == 0) continue;
-      int iy, iz;
-      row_yz(r, dims.y, inv_dy, iy, iz);
-      int y = lo.y + iy, z = lo.z + iz;
-      if (!fluid_row<GEOM>(L, y, z)) continue;
-      atomicAdd(L.g + (size_t)L.nx * (y + L.ny * z) + x,
-                make_float4((float)qx * inv, (float)qy * inv, (float)qz * inv, 0.f));
-    }
-  }
+  flush_box<GEOM>(L, lo, dims, ibox, 1.0f / S);
 }
 
 // Velocity at one marker gathered from the lattice (groups whose box does
@@ -535,35 +613,7 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
   float4* rec = vbox + BOX_CELLS;                                // [XFER_GROUP_MAX]
   Residues& R = *reinterpret_cast<Residues*>(rec + XFER_GROUP_MAX);
   if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
-  {
-    // the box of velocities row by row with asynchronous 16-byte copies
-    // (solid rows are written as zero); the force density there is cleared
-    // (consumed by this step's collision)
-    const int nrows = dims.y * dims.z;
-    const int nwarps = blockDim.x >> 5;
-    const RowSweep sw = row_sweep(dims.x);
-    const int rstep = nwarps * sw.rpw;
-    const float inv_dy = 1.0f / (float)dims.y;
-    const int xw0 = wrapi(lo.x, L.nx);
-    for (int ax = sw.ax; sw.on && ax < dims.x; ax += 32) {
-      const int x = box_x(xw0, ax, L.nx);
-      for (int r = (threadIdx.x >> 5) * sw.rpw + sw.sub; r < nrows; r += rstep) {
-        int iy, iz;
-        row_yz(r, dims.y, inv_dy, iy, iz);
-        int y = lo.y + iy, z = lo.z + iz;
-        float4* dst = vbox + r * dims.x + ax;
-        if (fluid_row<GEOM>(L, y, z)) {
-          const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(L.uw + gi) : "memory");
-          L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-          *dst = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
+  velocity_box_async<GEOM>(L, lo, dims, vbox);
   __syncthreads();
   // markers by residue of their first node's box index (-1: outside the box)
   int li[XFER_PER_THREAD];
@@ -585,39 +635,9 @@ __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const Mar
     pos[q] = atomicAdd(&R.cur[li[q] & 31], 1);
     rec[pos[q]] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  velocity_box_wait();
   __syncthreads();
-  {
-    // gather: lane r takes the w-th marker of residue r; the result replaces
-    // the marker's record
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int n = R.cnt[lane], st = R.start[lane];
-    for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
-      if (w >= n) continue;
-      const float4 A = rec[st + w];
-      float wx[4], wy[4], wz[4];
-      axis_weights(A.y, wx);
-      axis_weights(A.z, wy);
-      axis_weights(A.w, wz);
-      const int li0 = __float_as_int(A.x);
-      float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
-          const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
-          const float rx = fmaf(wx[3], v3.x, fmaf(wx[2], v2.x, fmaf(wx[1], v1.x, wx[0] * v0.x)));
-          const float ry = fmaf(wx[3], v3.y, fmaf(wx[2], v2.y, fmaf(wx[1], v1.y, wx[0] * v0.y)));
-          const float rz = fmaf(wx[3], v3.z, fmaf(wx[2], v2.z, fmaf(wx[1], v1.z, wx[0] * v0.z)));
-          const float wyz = wy[b] * wz[c];
-          ux = fmaf(wyz, rx, ux);
-          uy = fmaf(wyz, ry, uy);
-          uz = fmaf(wyz, rz, uz);
-        }
-      rec[st + w] = make_float4(ux, uy, uz, 0.f);
-    }
-  }
+  gather_records(vbox, dims, R, rec);
   __syncthreads();
   // results back in marker order: velocity, advection (FP64), stencil cache
 #pragma unroll

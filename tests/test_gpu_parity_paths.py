@@ -9,7 +9,12 @@ against the FP64 oracle through the C ABI:
   tiles, over even and odd steps;
 * the membrane force scatter in fixed point (taken once a previous step set
   the body's scale) and its float redo (taken when a contribution outgrows
-  that scale) (Sec. 2.2, Eqs. membrane-potential .. volumeEnergy).
+  that scale) (Sec. 2.2, Eqs. membrane-potential .. volumeEnergy);
+* the fused coupling kernel of membrane suspensions (interpolation, forces
+  and spreading per body between two collisions, two force-density
+  buffers), which ibm_lbm_step takes for chunks of 16 and 64 steps, against
+  the same steps run stage by stage with the separate kernels and against
+  the oracle.
 Tolerances as in test_gpu_parity.py."""
 import os
 import subprocess
@@ -106,3 +111,36 @@ def test_membrane_forces_overflow_redo(cuda_lib):
     scale = np.abs(Fo).max()
     assert scale > 1e-4
     assert np.abs(Fg - Fo).max() < 1e-4 * scale
+
+
+def test_fused_membrane_chunks_match_stages_and_oracle(cuda_lib):
+    """98 steps of deformed membranes in a tube through ibm_lbm_step (one
+    fused chunk of 64 steps, two of 16, two single steps) against the same
+    steps stage by stage, and against the FP64 oracle. Several groups add
+    into shared cells with float atomics, so the two GPU paths agree to
+    rounding (the bound of the serving identity test), not bit for bit."""
+    w = membrane_case()
+    w['lattice'] = dict(w['lattice'], body_force=[2e-6, 0, 0])
+    steps = 98
+    a = cuda_lib.Simulation.from_workload(w)
+    a.step(steps)
+    b = cuda_lib.Simulation.from_workload(w)
+    for _ in range(steps):
+        for st in (cuda_lib.STAGE_FORCES, cuda_lib.STAGE_SPREAD, cuda_lib.STAGE_COLLIDE, cuda_lib.STAGE_INTERP):
+            b.stage(st)
+    ua, ub = a.fields()[1], b.fields()[1]
+    Xa, Ua, Fa = a.markers()
+    Xb, Ub, Fb = b.markers()
+    from tests._cases import fluid_mask, rel_l2
+    fl = fluid_mask(w['lattice'])
+    assert rel_l2(ua[:, fl], ub[:, fl]) < 1e-6
+    assert np.abs(Xa - Xb).max() < 1e-7
+    assert np.abs(Fa - Fb).max() < 1e-4 * np.abs(Fb).max()
+    assert a.diagnostics()['steps'] == steps
+    ora = O.Oracle.from_workload(w)
+    ora.step(steps)
+    uo = ora.fields()[1]
+    Xo, _, Fo = ora.markers()
+    assert rel_l2(ua[:, fl], uo[:, fl]) < 1e-5
+    assert np.abs(Xa - Xo).max() < 1e-5
+    assert np.abs(Fa - Fo).max() < 1e-3 * np.abs(Fo).max()
