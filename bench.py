@@ -275,8 +275,32 @@ def aggregate(units_per_rank, max_seconds, n_ranks):
 # ----------------------------------------------------------------------------
 # reference arm and CPU baseline: the FP64 oracle as it stands
 # ----------------------------------------------------------------------------
-def time_oracle(w, steps, warmup=0):
+def host_cpu():
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith('Model name:'):
+                model = line.split(':', 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open('/proc/cpuinfo'):
+                if line.startswith('model name'):
+                    model = line.split(':', 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return dict(nproc=os.cpu_count(), model=model or 'unknown')
+
+
+def time_oracle(w, steps, warmup=0, threads=0):
+    """The FP64 oracle on `threads` host threads (0: all of them)."""
     import oracle as O
+    O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     t0 = time.perf_counter()
     o = O.Oracle.from_workload(w)
     setup = time.perf_counter() - t0
@@ -286,7 +310,7 @@ def time_oracle(w, steps, warmup=0):
     o.step(steps)
     dt = time.perf_counter() - t0
     N = w['lattice']['nx'] * w['lattice']['ny'] * w['lattice']['nz']
-    return dict(mlups=N * steps / dt / 1e6, seconds=dt, setup_s=setup, steps=steps)
+    return dict(mlups=N * steps / dt / 1e6, seconds=dt, setup_s=setup, steps=steps, threads=O.set_threads(0))
 
 
 def cpu_sample(name):
@@ -311,13 +335,16 @@ def run_reference(args):
     n = max(1, min(args.steps, args.ref_max_steps))
     wu = max(0, min(args.warmup, 3))
     r = time_oracle(w, n, warmup=wu)
+    cpu = host_cpu()
     line = dict(impl='reference', metric=METRIC, value=r['mlups'], unit=UNIT, n_gpus=args.gpus, steps=n,
                 warmup=wu, ms_per_step=1e3 * r['seconds'] / n, higher_is_better=True, scaling='weak',
                 vs_baseline=None, dtype='f64', data='synthetic',
                 config=dict(workload=w['label'], requested_steps=args.steps, lattice=[w['lattice'][k] for k in ('nx', 'ny', 'nz')],
                             markers=int(w['X'].shape[1]), bodies=len(w['bodies'])),
-                cpu_baseline=dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
-                                  sample=f'{n} full coupled step(s) of {w["label"]} on one host core (FP64 C oracle)'),
+                cpu_baseline=dict(value=r['mlups'], unit=UNIT, cores=r['threads'], kind='oracle',
+                                  sample=f'{n} full coupled step(s) of {w["label"]} on {r["threads"]} host threads '
+                                         f'(FP64 C oracle, OpenMP over its independent loops)',
+                                  nproc=cpu['nproc'], cpu_model=cpu['model']),
                 e2e=dict(value=r['mlups'], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -338,6 +365,36 @@ def kernels_per_step(w):
         if (w.get('morse') or {}).get('rc', 0) > 0:
             n += 10
     return n
+
+
+def production_launches(w, steps, fused):
+    """Kernels ibm_lbm_step launches for `steps` steps from an even AA step:
+    fused chunks of 64 (while more than 64 steps remain) or 16 steps (first
+    step's forces and spreading, then collide + fused kernel per step, the
+    last interpolation alone), the remaining steps one by one through the
+    separate kernels, and the conservation check. Without the fused path
+    every step takes the separate kernels."""
+    per_step = kernels_per_step(w)
+    if not fused:
+        return per_step * steps + 1
+    n, left = 0, steps
+    while left > 16:
+        c = 64 if left > 64 else 16
+        n += 2 + c + (c - 1) + 1
+        left -= c
+    return n + per_step * left + 1
+
+
+def fused_path(w, storage):
+    """Whether ibm_lbm_step takes the fused coupling kernel for workload w:
+    every marker in a membrane body, no Morse term (the library decides the
+    same at set_markers / step time)."""
+    bodies = w['bodies']
+    if not bodies or (w.get('morse') or {}).get('rc', 0) > 0:
+        return False
+    if any(b['kind'] != 0 for b in bodies):
+        return False
+    return sum(b['count'] for b in bodies) == w['X'].shape[1] and w['mesh']['rest_X'].shape[1] <= 1024
 
 
 def run_ours(args):
@@ -392,7 +449,9 @@ def run_ours(args):
     sim.set_timing(0)
     value = aggregate(N * args.steps, ms_max / 1e3, ws) / 1e6
 
-    # ---- roofline of the collide-stream kernel -------------------------------
+    # ---- roofline of the collide-stream kernel and of the whole step --------
+    # (the collide kernel is the same in the separate-kernel and the fused
+    # path; its duration comes from the event-per-stage run)
     sp = bytes_per_pop(storage)
     n_touch = touched_cells(lat, w['X'])
     alg_bytes = Nf * 38 * sp + n_touch * 24
@@ -400,11 +459,17 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / collide_s / 1e9
     step_alg = alg_bytes + M * 72
+    step_s = ms_max / 1e3 / args.steps
     roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
                 traffic=collide_traffic(storage), kernel='k_collide (fused collide-stream-force)',
                 peak_source=f'{peak_kind} hbm_gbs (burst copy)',
                 alg_bytes_per_launch=alg_bytes, step_alg_bytes=step_alg,
-                step_frac=(step_alg / (ms_max / 1e3 / args.steps) / 1e9) / peak)
+                step_alg_bytes_formula='N_f*38*s_p + N_touch*24 + M*72 (populations read+written once, force '
+                                       'density read and velocity written on touched cells, FP64 X read+written '
+                                       'and FP32 U, F per marker)',
+                step_achieved=step_alg / step_s / 1e9,
+                step_frac=(step_alg / step_s / 1e9) / peak)
+    fused = fused_path(w, storage)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     rho0 = np.ones(N)
@@ -435,9 +500,13 @@ def run_ours(args):
         oracle.build()
         ws_cpu = cpu_sample(args.workload)
         r = time_oracle(ws_cpu, 1)
-        cpu = dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
-                   sample=f'1 full coupled step of {ws_cpu["label"]} (FP64 C oracle, single thread, setup excluded)',
-                   seconds=r['seconds'])
+        r1 = time_oracle(ws_cpu, 1, threads=1)
+        hc = host_cpu()
+        cpu = dict(value=r['mlups'], unit=UNIT, cores=r['threads'], kind='oracle',
+                   sample=f'1 full coupled step of {ws_cpu["label"]} (FP64 C oracle, {r["threads"]} threads, '
+                          f'setup excluded)',
+                   seconds=r['seconds'], single_thread=dict(value=r1['mlups'], unit=UNIT, seconds=r1['seconds']),
+                   nproc=hc['nproc'], cpu_model=hc['model'])
 
     if rank == 0:
         tot = sum(stages[k] for k in ('forces_ms', 'spread_ms', 'collide_ms', 'interp_ms'))
@@ -454,6 +523,9 @@ def run_ours(args):
                         filaments=sum(1 for b in w['bodies'] if b['kind'] == 2), morse=w.get('morse'),
                         body_force=lat['body_force'][0], storage=storage, seed=w['seed'],
                         mflups_fluid=Nf * args.steps * ws / (ms_max / 1e3) / 1e6,
+                        production_path='collide + fused coupling kernel per step (membrane suspension)' if fused
+                        else 'separate kernels per stage',
+                        coupling_ms_per_step=ms_max / args.steps - split['collide_ms'],
                         staged_path_ms_per_step=staged_ms / args.steps,
                         stage_ms_per_step=split,
                         coupling_share=(split['spread_ms'] + split['interp_ms']) / max(1e-12, tot / max(1, stages['steps'])),
@@ -462,7 +534,7 @@ def run_ours(args):
             roofline=roof, cpu_baseline=cpu, e2e=e2e,
             clocks=dict(sm_mhz=clk['sm_mhz'], sm_max_mhz=clk['sm_max_mhz'], reasons=clk['reasons'],
                         samples=clk['samples']),
-            gpu_launches=kernels_per_step(w) * args.steps + 1,
+            gpu_launches=production_launches(w, args.steps, fused),
             diagnostics=dict(mass=diag['mass'], fluid_cells=diag['fluid_cells'], umax=diag['umax']),
             timed_stage_total_ms=tot)
         print(json.dumps(line), flush=True)
@@ -613,9 +685,11 @@ def run_serve(args):
         w0 = cases[0]
         k = 40
         r = time_oracle(w0, k)
-        cpu = dict(value=r['mlups'], unit=UNIT, cores=1, kind='oracle',
-                   sample=f'{k} coupled steps of serving case 0 ({w0["name"]}) on one host core (FP64 C oracle)',
-                   seconds=r['seconds'])
+        hc = host_cpu()
+        cpu = dict(value=r['mlups'], unit=UNIT, cores=r['threads'], kind='oracle',
+                   sample=f'{k} coupled steps of serving case 0 ({w0["name"]}) on {r["threads"]} host threads '
+                          f'(FP64 C oracle)',
+                   seconds=r['seconds'], nproc=hc['nproc'], cpu_model=hc['model'])
     if rank == 0:
         h2d = sum(w['X'].nbytes for w in cases)
         d2h = sum(w['N'] * 4 * 8 + w['X'].nbytes * 2 for w in cases)

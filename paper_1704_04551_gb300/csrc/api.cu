@@ -6,6 +6,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -356,6 +357,68 @@ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 V3 crs(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
 double dt3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// Orders items (triangles or edges) so that, in each run of 32 consecutive
+// items (one warp of the membrane force kernel), the vertices (and
+// triangles) an item reads and accumulates into in each of its roles differ
+// modulo 32: the warp's shared-memory accesses for one role then fall in
+// distinct banks. Greedy: each run takes the first remaining items whose
+// residues are all still free; a run that finds none completes with the
+// items of fewest clashes. Only the order changes, not the items.
+template <int R>
+std::vector<int> bank_order(const std::vector<std::array<int, R>>& keys) {
+  const int n = (int)keys.size();
+  std::vector<int> order;
+  order.reserve(n);
+  std::vector<char> taken(n, 0);
+  int left = n;
+  while (left > 0) {
+    uint32_t used[R] = {};
+    int in_run = 0;
+    for (int pass = 0; pass < 2 && in_run < 32 && in_run < left; ++pass) {
+      for (int i = 0; i < n && in_run < 32 && in_run < left; ++i) {
+        if (taken[i]) continue;
+        int clash = 0;
+        for (int r = 0; r < R; ++r) clash += (used[r] >> (keys[i][r] & 31)) & 1u;
+        if (pass == 0 && clash) continue;
+        taken[i] = 1;
+        order.push_back(i);
+        for (int r = 0; r < R; ++r) used[r] |= 1u << (keys[i][r] & 31);
+        ++in_run;
+      }
+    }
+    left -= in_run;
+  }
+  return order;
+}
+
+void order_for_banks(HostMesh& m) {
+  // triangles: their three vertices
+  std::vector<std::array<int, 3>> tk(m.tris.size());
+  for (size_t t = 0; t < m.tris.size(); ++t) tk[t] = {m.tris[t].x, m.tris[t].y, m.tris[t].z};
+  const std::vector<int> to = bank_order<3>(tk);
+  std::vector<int> new_of_t(m.tris.size());
+  std::vector<int4> tris(m.tris.size());
+  for (size_t i = 0; i < to.size(); ++i) {
+    tris[i] = m.tris[to[i]];
+    new_of_t[to[i]] = (int)i;
+  }
+  m.tris.swap(tris);
+  for (auto& et : m.edge_tris) et = make_int2(new_of_t[et.x], new_of_t[et.y]);
+  // edges: their four vertices and two triangles
+  std::vector<std::array<int, 6>> ek(m.edges.size());
+  for (size_t e = 0; e < m.edges.size(); ++e)
+    ek[e] = {m.edges[e].x, m.edges[e].y, m.edges[e].z, m.edges[e].w, m.edge_tris[e].x, m.edge_tris[e].y};
+  const std::vector<int> eo = bank_order<6>(ek);
+  std::vector<int4> edges(m.edges.size());
+  std::vector<int2> et(m.edges.size());
+  for (size_t i = 0; i < eo.size(); ++i) {
+    edges[i] = m.edges[eo[i]];
+    et[i] = m.edge_tris[eo[i]];
+  }
+  m.edges.swap(edges);
+  m.edge_tris.swap(et);
+}
+
 bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
   const int nv = mesh->n_vertices, nt = mesh->n_triangles;
   if (nv < 4 || nv > MAX_MESH_VERTICES || nt < 4 || !mesh->tris || !mesh->rest_X) {
@@ -399,6 +462,7 @@ bool build_mesh(const ibm_lbm_mesh* mesh, HostMesh& out, std::string& why) {
       why = "mesh: open boundary edge";
       return false;
     }
+  order_for_banks(out);
   out.edge_rest.resize(out.edges.size());
   for (size_t i = 0; i < out.edges.size(); ++i) {
     const int4 e = out.edges[i];

@@ -27,6 +27,19 @@
 
 namespace ibm {
 
+// Vertices a thread of the fused kernel advects (templates of up to
+// COUPLE_PER_THREAD * XFER_THREADS vertices take the fused path).
+constexpr int COUPLE_PER_THREAD = 2;
+
+// Byte offset of the counters in the fused kernel's shared memory.
+__host__ __device__ constexpr int couple_residues_offset(int nv, int nt) {
+  const int box = BOX_CELLS * 16;
+  const int forces = 36 * nv + 16 * nt;
+  const int spread = 36 * nv + 12 * BOX_CELLS + 2 * nv;
+  const int most = box > forces ? (box > spread ? box : spread) : (forces > spread ? forces : spread);
+  return (most + 15) / 16 * 16;
+}
+
 namespace {
 
 // Stencil of vertex v from the positions in shared memory (integer parts
@@ -51,67 +64,80 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   const int4 lo = box[0], dims = box[1];
   const bool in_box = dims.w != 0;
   float4* vbox = reinterpret_cast<float4*>(smem);
-  float4* rec = vbox + BOX_CELLS;                                 // [nv]
-  Residues& R = *reinterpret_cast<Residues*>(rec + nv);
+  Residues& R = *reinterpret_cast<Residues*>(smem + couple_residues_offset(nv, nt));
   // origin of the integer parts in shared memory: the first vertex's cell
   // before this step's advection (read before any thread writes the cache)
   const int3 o = make_int3(m.cell[G.first], m.cell[M + G.first], m.cell[2 * M + G.first]);
 
   // ---- 1. interpolation of step n and advection --------------------------
-  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
-  if (in_box) velocity_box_async<GEOM>(L, lo, dims, vbox);
-  __syncthreads();
-  int li[XFER_PER_THREAD], pos[XFER_PER_THREAD];
-#pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
-    li[q] = (in_box && j < G.count) ? box_index(m, G.first + j, lo, dims) : -1;
-    if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
+  // Each thread gathers for its own markers: the bank conflicts of the
+  // gather cost less here than the extra passes and barriers of sorting the
+  // markers by residue (measured); the new stencil of each marker is kept in
+  // registers until the velocity box, which the positions overwrite, is done.
+  if (in_box) {
+    velocity_box_async<GEOM>(L, lo, dims, vbox);
+    velocity_box_wait();
+    __syncthreads();
   }
-  __syncthreads();
-  residue_scan(R);
-  __syncthreads();
+  int cnew[COUPLE_PER_THREAD][3];
+  float fnew[COUPLE_PER_THREAD][3];
 #pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    pos[q] = -1;
-    if (li[q] < 0) continue;
-    const int k = G.first + threadIdx.x + q * XFER_THREADS;
-    pos[q] = atomicAdd(&R.cur[li[q] & 31], 1);
-    rec[pos[q]] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
-  }
-  velocity_box_wait();
-  __syncthreads();
-  gather_records(vbox, dims, R, rec);
-  __syncthreads();
-  const MembraneSmem S = MembraneSmem::at(smem, nv, nt);  // over the velocity box, which is done
-#pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
     const int j = threadIdx.x + q * XFER_THREADS;
     if (j >= G.count) continue;
     const int k = G.first + j;
+    Stencil st;
+    load_stencil(m, k, st);
+    double Xo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Xo[a] = m.X[a * M + k];
+    const int ox = st.bx - lo.x, oy = st.by - lo.y, oz = st.bz - lo.z;
     float3 u;
-    if (pos[q] >= 0) {
-      const float4 r = rec[pos[q]];
-      u = make_float3(r.x, r.y, r.z);
+    if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z) {
+      const int li0 = ox + dims.x * (oy + dims.y * oz);
+      float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
+          const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
+          const float rx = fmaf(st.wx[3], v3.x, fmaf(st.wx[2], v2.x, fmaf(st.wx[1], v1.x, st.wx[0] * v0.x)));
+          const float ry = fmaf(st.wx[3], v3.y, fmaf(st.wx[2], v2.y, fmaf(st.wx[1], v1.y, st.wx[0] * v0.y)));
+          const float rz = fmaf(st.wx[3], v3.z, fmaf(st.wx[2], v2.z, fmaf(st.wx[1], v1.z, st.wx[0] * v0.z)));
+          const float wyz = st.wy[b] * st.wz[c];
+          ux = fmaf(wyz, rx, ux);
+          uy = fmaf(wyz, ry, uy);
+          uz = fmaf(wyz, rz, uz);
+        }
+      u = make_float3(ux, uy, uz);
     } else {  // no box, or the stencil outside it
-      Stencil st;
-      load_stencil(m, k, st);
       u = gather_global<GEOM>(L, st, !in_box);
     }
     m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
     const float ua[3] = {u.x, u.y, u.z};
-    const int oa[3] = {o.x, o.y, o.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double Xn = m.X[a * M + k] + (double)ua[a];
+      const double Xn = Xo[a] + (double)ua[a];
       m.X[a * M + k] = Xn;
       const double fl = floor(Xn);
-      const int c = (int)fl;
-      const float f = (float)(Xn - fl);
-      m.cell[a * M + k] = c;
-      m.frac[a * M + k] = f;
-      S.sI[a * nv + j] = (float)(c - oa[a]);
-      S.sR[a * nv + j] = f;
+      cnew[q][a] = (int)fl;
+      fnew[q][a] = (float)(Xn - fl);
+      m.cell[a * M + k] = cnew[q][a];
+      m.frac[a * M + k] = fnew[q][a];
+    }
+  }
+  __syncthreads();  // the velocity box is done: the positions go over it
+  const MembraneSmem S = MembraneSmem::at(smem, nv, nt);
+  const int oa[3] = {o.x, o.y, o.z};
+#pragma unroll
+  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
+    const int j = threadIdx.x + q * XFER_THREADS;
+    if (j >= G.count) continue;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      S.sI[a * nv + j] = (float)(cnew[q][a] - oa[a]);
+      S.sR[a * nv + j] = fnew[q][a];
     }
   }
   __syncthreads();
@@ -209,9 +235,9 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
   if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
   __syncthreads();
-  int l2[XFER_PER_THREAD];
+  int l2[COUPLE_PER_THREAD];
 #pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
+  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
     const int v = threadIdx.x + q * XFER_THREADS;
     l2[q] = -1;
     if (v >= nv) continue;
@@ -225,7 +251,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   residue_scan(R);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q)
+  for (int q = 0; q < COUPLE_PER_THREAD; ++q)
     if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * XFER_THREADS);
   __syncthreads();
   {
@@ -258,22 +284,19 @@ __global__ void __launch_bounds__(XFER_THREADS, 2)
 }  // namespace
 
 // Shared memory of the fused kernel for a template of nv vertices: the
-// velocity box, one record per vertex, the counters. The forces' region
-// (positions, forces, normals, areas) and the spreading's (positions and
-// forces, fixed-point box, vertex order) must fit below the counters
-// (couple_fits); at 642 vertices the kernel takes 107 KiB, two blocks per SM.
+// largest of its three regions (the velocity box; the positions, forces,
+// normals and areas; the positions and forces, the fixed-point box and the
+// vertex order), then the counters. At 642 vertices: 96.5 KiB, two blocks
+// per SM; templates that need more than the interpolation kernel's shared
+// memory take the separate kernels.
 constexpr int COUPLE_SMEM_MAX = INTERP_SMEM;
 
 size_t couple_smem(const MeshDev& mesh) {
-  return (size_t)BOX_CELLS * sizeof(float4) + (size_t)mesh.nv * sizeof(float4) + RESIDUE_BYTES;
+  return (size_t)couple_residues_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;
 }
 
 bool couple_fits(const MeshDev& mesh) {
-  const size_t pos_forces = (size_t)9 * mesh.nv * sizeof(float);
-  const size_t normals = (size_t)4 * mesh.nt * sizeof(float);
-  const size_t spread = (size_t)3 * BOX_CELLS * sizeof(int) + (size_t)mesh.nv * sizeof(unsigned short);
-  const size_t below = couple_smem(mesh) - RESIDUE_BYTES;
-  return mesh.nv >= 1 && mesh.nv <= XFER_GROUP_MAX && pos_forces + normals <= below && pos_forces + spread <= below;
+  return mesh.nv >= 1 && mesh.nv <= COUPLE_PER_THREAD * XFER_THREADS && couple_smem(mesh) <= (size_t)COUPLE_SMEM_MAX;
 }
 
 cudaError_t couple_configure() {
