@@ -58,3 +58,26 @@ def membrane_case(n=40, R=16.0, cells=3, seed=21, deform=0.08):
     for b in w['bodies']:
         b.update(kBT_p=2e-3, k_b=1e-3, k_l=5e-3, k_g=4e-3, k_v=3e-3)
     return w
+
+
+# lattices wide enough for full 128-cell blocks, a ragged x block, several
+# 64-cell warps per row and many row blocks
+WIDE = {
+    'periodic': dict(nx=160, ny=40, nz=36, tau=0.8, geometry=0, body_force=[2e-6, -1e-6, 5e-7]),
+    'ywalls': dict(nx=160, ny=38, nz=36, tau=0.7, geometry=1, wall_u=[-0.015, 0.02], body_force=[1e-6, 0, 0]),
+    'tube': dict(nx=160, ny=40, nz=40, tau=1.0, geometry=2, tube_radius=18.5, body_force=[3e-6, 0, 0]),
+}
+
+
+def wide_tracers(lat, M, seed):
+    """Marker positions in the fluid of a WIDE lattice, with forces."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape(lat)
+    if lat['geometry'] == 2:
+        r = (lat['tube_radius'] - 1.0) * np.sqrt(rng.random(M))
+        th = 2 * np.pi * rng.random(M)
+        X = np.stack([nx * rng.random(M), (ny - 1) / 2 + r * np.cos(th), (nz - 1) / 2 + r * np.sin(th)])
+    else:
+        X = np.stack([nx * rng.random(M), (ny - 1) * rng.random(M), nz * rng.random(M)])
+    F = 2e-3 * (2 * rng.random((3, M)) - 1)
+    return X, F

@@ -10,6 +10,8 @@ against the FP64 oracle through the C ABI:
 * the membrane force scatter in fixed point (taken once a previous step set
   the body's scale) and its float redo (taken when a contribution outgrows
   that scale) (Sec. 2.2, Eqs. membrane-potential .. volumeEnergy);
+* the two-cells-per-thread collide of the half-precision formats, bit for
+  bit against a build that keeps one cell per thread (IBM_HALF_PER_CELL);
 * the fused coupling kernel of membrane suspensions (interpolation, forces
   and spreading per body between two collisions, two force-density
   buffers), which ibm_lbm_step takes for chunks of 16 and 64 steps, against
@@ -25,37 +27,17 @@ import pytest
 
 import oracle as O
 from paper_1704_04551_gb300 import inputs as I
-from tests._cases import membrane_case, shape
+from tests._cases import WIDE, membrane_case, shape, wide_tracers
 from tests._collide_parity import check_collide_parity
 
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-WIDE = {
-    'periodic': dict(nx=160, ny=40, nz=36, tau=0.8, geometry=0, body_force=[2e-6, -1e-6, 5e-7]),
-    'ywalls': dict(nx=160, ny=38, nz=36, tau=0.7, geometry=1, wall_u=[-0.015, 0.02], body_force=[1e-6, 0, 0]),
-    'tube': dict(nx=160, ny=40, nz=40, tau=1.0, geometry=2, tube_radius=18.5, body_force=[3e-6, 0, 0]),
-}
-
-
-def _tracers(lat, M, seed):
-    rng = np.random.default_rng(seed)
-    nx, ny, nz = shape(lat)
-    if lat['geometry'] == 2:
-        r = (lat['tube_radius'] - 1.0) * np.sqrt(rng.random(M))
-        th = 2 * np.pi * rng.random(M)
-        X = np.stack([nx * rng.random(M), (ny - 1) / 2 + r * np.cos(th), (nz - 1) / 2 + r * np.sin(th)])
-    else:
-        X = np.stack([nx * rng.random(M), (ny - 1) * rng.random(M), nz * rng.random(M)])
-    F = 2e-3 * (2 * rng.random((3, M)) - 1)
-    return X, F
-
-
 @pytest.mark.parametrize('geom', list(WIDE))
 def test_collide_wide_lattice_with_force_density(cuda_lib, geom):
     lat = WIDE[geom]
-    check_collide_parity(cuda_lib, lat, steps=3, seed=13, markers=_tracers(lat, 3000, 14))
+    check_collide_parity(cuda_lib, lat, steps=3, seed=13, markers=wide_tracers(lat, 3000, 14))
 
 
 def test_collide_64bit_offsets_variant(cuda_lib):
@@ -70,6 +52,31 @@ def test_collide_64bit_offsets_variant(cuda_lib):
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count(' ok ') == 3, r.stdout
+
+
+@pytest.mark.parametrize('storage', ['f16', 'bf16'])
+def test_half_pair_collide_bitwise_equal_to_one_cell(cuda_lib, storage, tmp_path):
+    """The paired half-precision collide does the one-cell arithmetic and
+    stores the same 16-bit values: populations, densities and velocities
+    after three coupled stages on the wide lattices (rows of 160 cells: full
+    and partial warps, the periodic wrap of x, warp-edge half stores) equal
+    those of the one-cell build exactly."""
+    from paper_1704_04551_gb300 import build
+    from tests._collide_parity import run_stages
+    out = os.path.join(build.BUILD, 'halfcell', 'libibmlbm.so')
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    build.build(extra=['-DIBM_HALF_PER_CELL'], out=out)
+    dump = str(tmp_path / 'onecell.npz')
+    env = dict(os.environ, IBM_LBM_LIBRARY=out, PYTHONPATH=ROOT + os.pathsep + os.environ.get('PYTHONPATH', ''))
+    r = subprocess.run([sys.executable, '-m', 'tests._collide_parity', 'dump', storage, dump], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+    ref = np.load(dump)
+    for geom, lat in WIDE.items():
+        f, rho, u = run_stages(cuda_lib, lat, storage, 3, 17, wide_tracers(lat, 2000, 18))
+        assert np.array_equal(f, ref[geom + '_f']), geom
+        assert np.array_equal(rho, ref[geom + '_rho']), geom
+        assert np.array_equal(u, ref[geom + '_u']), geom
 
 
 def test_membrane_forces_fixed_point_after_steps(cuda_lib):
