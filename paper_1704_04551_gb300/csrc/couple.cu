@@ -93,27 +93,10 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
     for (int a = 0; a < 3; ++a) Xo[a] = m.X[a * M + k];
     const int ox = st.bx - lo.x, oy = st.by - lo.y, oz = st.bz - lo.z;
     float3 u;
-    if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z) {
-      const int li0 = ox + dims.x * (oy + dims.y * oz);
-      float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
-          const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
-          const float rx = fmaf(st.wx[3], v3.x, fmaf(st.wx[2], v2.x, fmaf(st.wx[1], v1.x, st.wx[0] * v0.x)));
-          const float ry = fmaf(st.wx[3], v3.y, fmaf(st.wx[2], v2.y, fmaf(st.wx[1], v1.y, st.wx[0] * v0.y)));
-          const float rz = fmaf(st.wx[3], v3.z, fmaf(st.wx[2], v2.z, fmaf(st.wx[1], v1.z, st.wx[0] * v0.z)));
-          const float wyz = st.wy[b] * st.wz[c];
-          ux = fmaf(wyz, rx, ux);
-          uy = fmaf(wyz, ry, uy);
-          uz = fmaf(wyz, rz, uz);
-        }
-      u = make_float3(ux, uy, uz);
-    } else {  // no box, or the stencil outside it
+    if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z)
+      u = box_gather(vbox, dims, st, ox, oy, oz);
+    else  // no box, or the stencil outside it
       u = gather_global<GEOM>(L, st, !in_box);
-    }
     m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
     const float ua[3] = {u.x, u.y, u.z};
 #pragma unroll
@@ -289,7 +272,7 @@ __global__ void __launch_bounds__(XFER_THREADS, 2)
 // vertex order), then the counters. At 642 vertices: 96.5 KiB, two blocks
 // per SM; templates that need more than the interpolation kernel's shared
 // memory take the separate kernels.
-constexpr int COUPLE_SMEM_MAX = INTERP_SMEM;
+constexpr int COUPLE_SMEM_MAX = BOX_CELLS * 16 + XFER_GROUP_MAX * 16 + RESIDUE_BYTES;
 
 size_t couple_smem(const MeshDev& mesh) {
   return (size_t)couple_residues_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;

@@ -46,22 +46,6 @@ __global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_col
   collide_cell<S, ODD, GEOM, DENSE, IDX32>(L, rows[r], x);
 }
 
-// The half-precision formats, two cells per thread (collide_pair): each warp
-// takes 64 consecutive cells of one fluid row, four warps per block; the
-// grid is one-dimensional over (row, 64-cell chunk).
-constexpr int PAIR_WARPS = 4;
-// (two cells' values in flight per thread: 4 blocks of 4 warps per SM keep
-// as many bytes in flight as 8 blocks of the one-cell kernel, without spills)
-template <int S, int ODD, int GEOM, bool DENSE>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 4)
-    k_collide_pair(LatticeDev L, const RowInfo* __restrict__ rows, int n_rows, int nxw) {
-  const int gw = blockIdx.x * PAIR_WARPS + (threadIdx.x >> 5);
-  const int r = gw / nxw, chunk = gw - r * nxw;
-  if (r >= n_rows) return;  // whole warp
-  const int x0 = chunk * 64 + 2 * (threadIdx.x & 31);
-  collide_pair<S, ODD, GEOM, DENSE>(L, rows[r], x0, x0 < L.nx);
-}
-
 // Equilibrium initialisation from the moments in uw (ux, uy, uz, rho - 1).
 template <int S, int GEOM>
 __global__ void k_init_equilibrium(LatticeDev L) {
@@ -227,24 +211,6 @@ inline unsigned blocks_for(int n) { return (unsigned)((n + 255) / 256); }
 
 template <int S, int GEOM>
 void launch_collide_g(const LatticeDev& L, const RowInfo* rows, int n_rows, bool odd, bool dense, cudaStream_t st) {
-#ifndef IBM_HALF_PER_CELL
-  if constexpr (S != STORE_F32) {
-    // two cells per thread when rows hold an even number of cells (and the
-    // 32-bit element offsets hold); a build with IBM_HALF_PER_CELL keeps one
-    // cell per thread, so that the tests can compare the two bit for bit
-    if (L.nx % 2 == 0 && (unsigned long long)Q * (unsigned long long)L.N < (1ull << 32)) {
-      const int nxw = (L.nx + 63) / 64;
-      const unsigned long long warps = (unsigned long long)n_rows * nxw;
-      const dim3 grid((unsigned)((warps + PAIR_WARPS - 1) / PAIR_WARPS));
-      const int t = PAIR_WARPS * 32;
-      if (odd && dense) k_collide_pair<S, 1, GEOM, true><<<grid, t, 0, st>>>(L, rows, n_rows, nxw);
-      else if (odd) k_collide_pair<S, 1, GEOM, false><<<grid, t, 0, st>>>(L, rows, n_rows, nxw);
-      else if (dense) k_collide_pair<S, 0, GEOM, true><<<grid, t, 0, st>>>(L, rows, n_rows, nxw);
-      else k_collide_pair<S, 0, GEOM, false><<<grid, t, 0, st>>>(L, rows, n_rows, nxw);
-      return;
-    }
-  }
-#endif
   const int tx = L.nx >= COLLIDE_THREADS ? COLLIDE_THREADS : ((L.nx + 31) / 32) * 32;
   const int ty = COLLIDE_THREADS / tx;
   const int nxb = (L.nx + tx - 1) / tx;

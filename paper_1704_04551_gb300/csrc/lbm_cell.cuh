@@ -239,129 +239,4 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
 }
 
 
-// Two adjacent cells (x0, x0 + 1), x0 even, of a fluid row, for the
-// half-precision formats: the 19 slots of the pair move as 32-bit words of
-// two 16-bit values, which halves the load and store instructions (the
-// half-precision collide is bound by instruction issue, not bandwidth).
-// Requires nx even (words do not straddle rows) and 19 N < 2^32 (32-bit
-// element offsets). Lanes of a warp hold consecutive pairs of one row.
-//   loads: a slot whose source is the same x pair (even step, or odd step
-//   with c_x = 0, or bounced) is one aligned word; an odd-step source at
-//   x -+ 1 straddles two aligned words, combined with one byte permute;
-//   stores: an odd-step destination at x +- 1 straddles two words, each half
-//   coming from a neighbouring pair: the lane takes the missing half from
-//   the adjacent lane by a shuffle and writes whole words; at a warp edge or
-//   across the periodic wrap of x the halves are written as 16-bit values.
-// Both cells share their row, so their (y, z) neighbours and bounce-back
-// pattern are the same; x neighbours are never solid.
-template <int S, int ODD, int GEOM, bool DENSE>
-__device__ __forceinline__ void collide_pair(const LatticeDev& L, const RowInfo& R, int x0, bool active) {
-  static_assert(S != STORE_F32, "pairs are for the 16-bit formats");
-  using T = typename Pop<S>::T;
-  const int lane = threadIdx.x & 31;
-  const int nx = L.nx;
-  const unsigned N = (unsigned)L.N;
-  const int idx0 = R.base + x0;  // even: rows hold an even number of cells
-  Cell c;
-  c.x = x0;
-  c.y = R.y;
-  c.smask = (unsigned)R.smask;
-  c.oxp = 0;
-  c.oxm = 0;  // x offsets are handled by the word arithmetic below
-  c.oyp = R.oyp; c.oym = R.oym; c.ozp = R.ozp; c.ozm = R.ozm;
-  uint32_t* W = reinterpret_cast<uint32_t*>(L.pop);
-  // word index of element e (e even)
-  auto word = [&](unsigned e) -> uint32_t* { return W + (e >> 1); };
-  const int xm2 = (x0 == 0) ? nx - 2 : -2;      // x0 - 2, wrapped within the row
-  const int xp2 = (x0 + 2 == nx) ? 2 - nx : 2;  // x0 + 2, wrapped within the row
-  // element offset of the (y, z) part of the neighbour x + s c_i
-  auto yz_off = [&](int i, int s) {
-    const int dy = s * cy(i), dz = s * cz(i);
-    return (dy > 0 ? c.oyp : (dy < 0 ? c.oym : 0)) + (dz > 0 ? c.ozp : (dz < 0 ? c.ozm : 0));
-  };
-
-  uint32_t w[Q];
-#pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    w[j] = 0u;
-    if (!active) continue;
-    if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1))) {
-      w[j] = *word((unsigned)j * N + (unsigned)idx0);
-    } else {
-      const unsigned e = (unsigned)opp(j) * N + (unsigned)(idx0 + yz_off(j, -1));
-      if (cx(j) == 0) {
-        w[j] = *word(e);
-      } else if (cx(j) > 0) {  // sources x0 - 1, x0
-        w[j] = __byte_perm(*word(e + (unsigned)xm2), *word(e), 0x5432);
-      } else {  // sources x0 + 1, x0 + 2
-        w[j] = __byte_perm(*word(e), *word(e + (unsigned)xp2), 0x5432);
-      }
-    }
-  }
-  // the two cells in turn: unpack a half of every word, collide, and put
-  // the result back into the same half of word i (result i is stored from
-  // word i below)
-  const int tile = R.trow + (x0 >> TILE_X_SHIFT);
-  float rho2[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    float d[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      const unsigned short h = (unsigned short)(q == 0 ? (w[j] & 0xffffu) : (w[j] >> 16));
-      if constexpr (S == STORE_F16) d[j] = __half2float(__ushort_as_half(h));
-      else d[j] = __bfloat162float(__ushort_as_bfloat16(h));
-    }
-    rho2[q] = 1.0f;
-    if (active) rho2[q] = relax_cell<S, DENSE>(L, d, idx0 + q, tile);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float v = d[i];
-      if (GEOM == GEOM_YWALLS && i != 0 && cx(i) != 0 && nb_solid(c, i, +1)) {
-        // bounced into slot opp(i): the half-precision scale of that slot
-        const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
-        v -= dev_scale(opp(i)) * 6.0f * wgt(i) * rho2[q] * (float)cx(i) * uw;
-      }
-      unsigned short h;
-      if constexpr (S == STORE_F16) h = __half_as_ushort(__float2half_rn(v));
-      else h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-      w[i] = q == 0 ? ((w[i] & 0xffff0000u) | h) : ((w[i] & 0xffffu) | ((uint32_t)h << 16));
-    }
-  }
-  // streaming with half-way bounce-back
-  const bool prev_ok = lane > 0 && x0 > 0;                 // lane - 1 holds x0 - 2
-  const bool next_ok = lane < 31 && x0 + 2 < nx;           // lane + 1 holds x0 + 2 (if active)
-  unsigned short* H = reinterpret_cast<unsigned short*>(L.pop);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const uint32_t v = w[i];
-    const bool sol = (GEOM != GEOM_PERIODIC) && i != 0 && nb_solid(c, i, +1);
-    if (!ODD || i == 0 || sol || cx(i) == 0) {
-      if (!active) continue;
-      const unsigned e = (!ODD || i == 0 || sol) ? (unsigned)opp(i) * N + (unsigned)idx0
-                                                 : (unsigned)i * N + (unsigned)(idx0 + yz_off(i, +1));
-      *word(e) = v;
-      continue;
-    }
-    const unsigned e = (unsigned)i * N + (unsigned)(idx0 + yz_off(i, +1));
-    if (cx(i) > 0) {
-      // x0 -> x0 + 1 (high half of the word at x0), x0 + 1 -> x0 + 2 (low
-      // half of the word at x0 + 2); the low half at x0 comes from x0 - 1
-      const uint32_t prev_hi = __shfl_up_sync(0xffffffffu, v, 1) >> 16;
-      if (!active) continue;
-      if (prev_ok) *word(e) = (prev_hi & 0xffffu) | (v << 16);
-      else H[e + 1] = (unsigned short)(v & 0xffffu);
-      if (!next_ok) H[e + (unsigned)xp2] = (unsigned short)(v >> 16);
-    } else {
-      // x0 -> x0 - 1 (high half of the word at x0 - 2), x0 + 1 -> x0 (low
-      // half of the word at x0); the high half at x0 comes from x0 + 2
-      const uint32_t next_lo = __shfl_down_sync(0xffffffffu, v, 1) & 0xffffu;
-      if (!active) continue;
-      if (next_ok) *word(e) = (v >> 16) | (next_lo << 16);
-      else H[e] = (unsigned short)(v >> 16);
-      if (!prev_ok) H[e + (unsigned)xm2 + 1] = (unsigned short)(v & 0xffffu);
-    }
-  }
-}
-
 }  // namespace ibm

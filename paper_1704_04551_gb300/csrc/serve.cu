@@ -141,6 +141,36 @@ __global__ void __launch_bounds__(SERVE_XFER_THREADS, 2) k_interpolate_b(const C
   }
 }
 
+// The same for chunks of fewer than LANE_MAX_GROUPS groups (four lanes per
+// marker).
+__global__ void __launch_bounds__(LANE_THREADS, 1) k_spread_bl(const CaseDev* cases, const Item* items) {
+  extern __shared__ __align__(16) int ibox_l[];
+  const Item it = items[blockIdx.x];
+  const CaseDev& C = cases[it.c];
+  if (!C.active) return;
+  const LatticeDev L = case_lattice(C);
+  int4* box = C.boxes + 2 * it.i;
+  switch (L.geometry) {
+    case GEOM_PERIODIC: spread_group_lanes<GEOM_PERIODIC>(L, C.m, C.groups[it.i], box, ibox_l); break;
+    case GEOM_YWALLS: spread_group_lanes<GEOM_YWALLS>(L, C.m, C.groups[it.i], box, ibox_l); break;
+    default: spread_group_lanes<GEOM_TUBE>(L, C.m, C.groups[it.i], box, ibox_l); break;
+  }
+}
+
+__global__ void __launch_bounds__(LANE_THREADS, 1) k_interpolate_bl(const CaseDev* cases, const Item* items) {
+  extern __shared__ __align__(16) unsigned char fbox_l[];
+  const Item it = items[blockIdx.x];
+  const CaseDev& C = cases[it.c];
+  if (!C.active) return;
+  const LatticeDev L = case_lattice(C);
+  const int4* box = C.boxes + 2 * it.i;
+  switch (L.geometry) {
+    case GEOM_PERIODIC: interpolate_group_lanes<GEOM_PERIODIC>(L, C.m, C.groups[it.i], box, fbox_l); break;
+    case GEOM_YWALLS: interpolate_group_lanes<GEOM_YWALLS>(L, C.m, C.groups[it.i], box, fbox_l); break;
+    default: interpolate_group_lanes<GEOM_TUBE>(L, C.m, C.groups[it.i], box, fbox_l); break;
+  }
+}
+
 // One warp per (case, row) segment of 32 cells. Cases are admitted only at
 // chunk boundaries and every chunk has an even number of steps, so all
 // running cases share the AA parity of a step and it is a template argument;
@@ -410,6 +440,7 @@ int rebuild(ibm_lbm_server_t* s) {
     s->graph = nullptr;
   }
   cudaGraph_t g = nullptr;
+  const bool lanes = s->n_groups < LANE_MAX_GROUPS;
   SCUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   for (int step = 0; step < s->cfg.chunk_steps; ++step) {
     k_book_begin<<<(n + 127) / 128, 128, 0, s->stream>>>(s->d_cases, n);
@@ -417,7 +448,10 @@ int rebuild(ibm_lbm_server_t* s) {
     if (s->n_rigid) k_rigid_b<<<s->n_rigid, RIGID_THREADS, 0, s->stream>>>(s->d_cases, s->d_rigid);
     if (s->n_membranes)
       k_membranes_b<<<s->n_membranes, MEMBRANE_THREADS, s->membrane_smem, s->stream>>>(s->d_cases, s->d_membranes);
-    if (s->n_groups) k_spread_b<<<s->n_groups, SERVE_XFER_THREADS, SPREAD_SMEM, s->stream>>>(s->d_cases, s->d_groups);
+    if (s->n_groups && lanes)
+      k_spread_bl<<<s->n_groups, LANE_THREADS, SPREAD_LANES_SMEM, s->stream>>>(s->d_cases, s->d_groups);
+    else if (s->n_groups)
+      k_spread_b<<<s->n_groups, SERVE_XFER_THREADS, SPREAD_SMEM, s->stream>>>(s->d_cases, s->d_groups);
     for (int g = 0; g < 3; ++g) {
       const int first = s->geom_first[g], n_items = s->geom_first[g + 1] - first;
       if (n_items == 0) continue;
@@ -435,7 +469,9 @@ int rebuild(ibm_lbm_server_t* s) {
         default: k_collide_b<1, GEOM_TUBE><<<grid, block, 0, s->stream>>>(s->d_cases, items, n_items, nxb); break;
       }
     }
-    if (s->n_groups)
+    if (s->n_groups && lanes)
+      k_interpolate_bl<<<s->n_groups, LANE_THREADS, INTERP_SMEM, s->stream>>>(s->d_cases, s->d_groups);
+    else if (s->n_groups)
       k_interpolate_b<<<s->n_groups, SERVE_XFER_THREADS, INTERP_SMEM, s->stream>>>(s->d_cases, s->d_groups);
     k_book_end<<<(n + 127) / 128, 128, 0, s->stream>>>(s->d_cases, n);
   }
@@ -513,7 +549,9 @@ static int impl_ibm_lbm_server_create(const ibm_lbm_server_config* cfg, const ib
     return IBM_LBM_E_NOMEM;
   }
   if (cudaFuncSetAttribute(k_spread_b, cudaFuncAttributeMaxDynamicSharedMemorySize, SPREAD_SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(k_interpolate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, INTERP_SMEM) != cudaSuccess) {
+      cudaFuncSetAttribute(k_interpolate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, INTERP_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_spread_bl, cudaFuncAttributeMaxDynamicSharedMemorySize, SPREAD_LANES_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_interpolate_bl, cudaFuncAttributeMaxDynamicSharedMemorySize, INTERP_SMEM) != cudaSuccess) {
     cudaGetLastError();
     ibm_lbm_server_destroy(s);
     return IBM_LBM_E_CUDA;

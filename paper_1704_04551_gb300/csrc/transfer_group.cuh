@@ -19,11 +19,14 @@
 // interpolation kernel refreshes right after advecting each marker; the only
 // FP64 arithmetic left is that advection.
 //
-// One thread block per marker group (a body, or a run of tracers), one
-// thread per marker: a thread computes its marker's 12 weights once and
-// visits the 64 stencil nodes itself; which marker a lane takes is chosen
-// so that a warp's shared-memory accesses fall in distinct banks (see
-// Residues below). The block bounds the group's stencils
+// One thread block per marker group (a body, or a run of tracers). Launches
+// of many groups (several blocks per SM) take one thread per marker: a
+// thread computes its marker's 12 weights once and visits the 64 stencil
+// nodes itself; which marker a lane takes is chosen so that a warp's
+// shared-memory accesses fall in distinct banks (see Residues below).
+// Launches of few groups are bound by the latency of one block's passes:
+// they take larger blocks and four lanes per marker, lane a visiting the
+// stencil's x column a (the *_lanes functions). The block bounds the group's stencils
 // with a box; when the box fits in shared memory (BOX_CELLS cells):
 //   spreading accumulates there in 32-bit fixed point (native integer
 //   shared-memory atomics; the sum does not depend on the order of the
@@ -54,11 +57,18 @@ constexpr int BOX_CELLS = 6144;     // shared-memory box limit (cells)
 constexpr int XFER_GROUP_MAX = 1024;  // markers per group (records in shared memory)
 constexpr int XFER_PER_THREAD = (XFER_GROUP_MAX + XFER_THREADS - 1) / XFER_THREADS;
 constexpr int RESIDUE_BYTES = 512;   // the counting sort's counters (struct Residues)
+// Launches of fewer groups than this take the four-lanes-per-marker
+// functions in blocks of LANE_THREADS: with at most a few blocks per SM the
+// time of one block's passes decides, not the issue rate of many.
+constexpr int LANE_MAX_GROUPS = 512;
+constexpr int LANE_THREADS = 1024;
 // fixed-point sums [3][vol], two float4 records per marker, counters
 constexpr int SPREAD_SMEM =
     3 * BOX_CELLS * (int)sizeof(int) + 2 * XFER_GROUP_MAX * (int)sizeof(float4) + RESIDUE_BYTES;
-// velocities [vol] float4, one float4 record per marker, counters
-constexpr int INTERP_SMEM = BOX_CELLS * (int)sizeof(float4) + XFER_GROUP_MAX * (int)sizeof(float4) + RESIDUE_BYTES;
+// velocities [vol] float4
+constexpr int INTERP_SMEM = BOX_CELLS * (int)sizeof(float4);
+// fixed-point sums [3][vol] (four lanes per marker: no marker records)
+constexpr int SPREAD_LANES_SMEM = 3 * BOX_CELLS * (int)sizeof(int);
 
 // The four delta weights of one axis for a marker at fractional offset f.
 __device__ __forceinline__ void axis_weights(float f, float w[4]) {
@@ -68,6 +78,14 @@ __device__ __forceinline__ void axis_weights(float f, float w[4]) {
   w[1] = fmaf(0.25f, c, 0.25f);
   w[2] = fmaf(0.25f, s, 0.25f);
   w[3] = fmaf(-0.25f, c, 0.25f);
+}
+
+// Weight of node a (0..3) of one axis: entry a of axis_weights, computed
+// alone (a lane that handles one node of each x column).
+__device__ __forceinline__ float axis_weight(float f, int a) {
+  float s, c;
+  sincospif(0.5f * f, &s, &c);
+  return fmaf((a == 0 || a == 3) ? -0.25f : 0.25f, (a & 1) ? c : s, 0.25f);
 }
 
 // Stencil of one marker: first node (unwrapped) on each axis and the
@@ -432,36 +450,26 @@ __device__ __forceinline__ void velocity_box_async(const LatticeDev& L, int4 lo,
 }
 __device__ __forceinline__ void velocity_box_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Velocity at every marker of the records (li0, fractional offsets): lane r
-// takes the w-th marker of residue r; each result (u, 0) replaces its record.
-__device__ __forceinline__ void gather_records(const float4* vbox, int4 dims, const Residues& R, float4* rec) {
-  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int n = R.cnt[lane], st = R.start[lane];
-  for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
-    if (w >= n) continue;
-    const float4 A = rec[st + w];
-    float wx[4], wy[4], wz[4];
-    axis_weights(A.y, wx);
-    axis_weights(A.z, wy);
-    axis_weights(A.w, wz);
-    const int li0 = __float_as_int(A.x);
-    float ux = 0.f, uy = 0.f, uz = 0.f;
+// Velocity at a marker whose 4^3 stencil lies in the box (first node at
+// box offsets ox, oy, oz), gathered from the shared-memory box.
+__device__ __forceinline__ float3 box_gather(const float4* vbox, int4 dims, const Stencil& st, int ox, int oy, int oz) {
+  const int li0 = ox + dims.x * (oy + dims.y * oz);
+  float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+  for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
-        const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
-        const float rx = fmaf(wx[3], v3.x, fmaf(wx[2], v2.x, fmaf(wx[1], v1.x, wx[0] * v0.x)));
-        const float ry = fmaf(wx[3], v3.y, fmaf(wx[2], v2.y, fmaf(wx[1], v1.y, wx[0] * v0.y)));
-        const float rz = fmaf(wx[3], v3.z, fmaf(wx[2], v2.z, fmaf(wx[1], v1.z, wx[0] * v0.z)));
-        const float wyz = wy[b] * wz[c];
-        ux = fmaf(wyz, rx, ux);
-        uy = fmaf(wyz, ry, uy);
-        uz = fmaf(wyz, rz, uz);
-      }
-    rec[st + w] = make_float4(ux, uy, uz, 0.f);
-  }
+    for (int b = 0; b < 4; ++b) {
+      const float4* p = vbox + li0 + dims.x * (b + dims.y * c);
+      const float4 v0 = p[0], v1 = p[1], v2 = p[2], v3 = p[3];
+      const float rx = fmaf(st.wx[3], v3.x, fmaf(st.wx[2], v2.x, fmaf(st.wx[1], v1.x, st.wx[0] * v0.x)));
+      const float ry = fmaf(st.wx[3], v3.y, fmaf(st.wx[2], v2.y, fmaf(st.wx[1], v1.y, st.wx[0] * v0.y)));
+      const float rz = fmaf(st.wx[3], v3.z, fmaf(st.wx[2], v2.z, fmaf(st.wx[1], v1.z, st.wx[0] * v0.z)));
+      const float wyz = st.wy[b] * st.wz[c];
+      ux = fmaf(wyz, rx, ux);
+      uy = fmaf(wyz, ry, uy);
+      uz = fmaf(wyz, rz, uz);
+    }
+  return make_float3(ux, uy, uz);
 }
 
 // Spreading of one marker group by the whole thread block; box_out receives
@@ -512,7 +520,7 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
   int li[XFER_PER_THREAD];
 #pragma unroll
   for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
+    const int j = threadIdx.x + q * blockDim.x;  // blockDim.x >= XFER_THREADS
     li[q] = j < G.count ? box_index(m, G.first + j, lo, dims) : -1;  // inside by construction of the box
     if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
   }
@@ -522,7 +530,7 @@ __device__ __forceinline__ void spread_group(const LatticeDev& L, const MarkersD
 #pragma unroll
   for (int q = 0; q < XFER_PER_THREAD; ++q) {
     if (li[q] < 0) continue;
-    const int k = G.first + threadIdx.x + q * XFER_THREADS;
+    const int k = G.first + threadIdx.x + q * blockDim.x;
     const int pos = atomicAdd(&R.cur[li[q] & 31], 1);
     const float4 F = m.F[k];
     rec[pos] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
@@ -577,85 +585,231 @@ __device__ __noinline__ float3 gather_global(const LatticeDev& L, const Stencil&
   return make_float3(ux, uy, uz);
 }
 
-// Advection of marker k by U (FP64) and the stencil cache of the new position.
-__device__ __forceinline__ void advect_marker(const MarkersDev& m, int k, float ux, float uy, float uz) {
-  const size_t M = (size_t)m.M;
-  const float ua[3] = {ux, uy, uz};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double Xn = m.X[a * M + k] + (double)ua[a];
-    m.X[a * M + k] = Xn;
-    cache_coord(m, a * M + k, Xn);
-  }
-}
-
-// Interpolation and advection of one marker group by the whole thread block.
-// smem: INTERP_SMEM bytes (velocity box, then the marker records).
+// Interpolation and advection of one marker group by the whole thread block:
+// the velocity box is loaded once, then each thread gathers for its own
+// markers (the bank conflicts of the gather cost less than sorting the
+// markers by residue, which pays off for the atomics of the spreading only)
+// and advects them. smem: INTERP_SMEM bytes (the velocity box).
 template <int GEOM>
 __device__ __forceinline__ void interpolate_group(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
                                                   const int4* box_in, unsigned char* smem) {
   const int4 lo = box_in[0], dims = box_in[1];
   const size_t M = (size_t)m.M;
   const bool moves = !(G.flags & GROUP_FIXED);
-  if (dims.w == 0) {
-    // no box: every marker gathers from the lattice and clears what it visits
-    for (int j = threadIdx.x; j < G.count; j += blockDim.x) {
-      const int k = G.first + j;
-      Stencil s;
-      load_stencil(m, k, s);
-      const float3 u = gather_global<GEOM>(L, s, true);
-      m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
-      if (moves) advect_marker(m, k, u.x, u.y, u.z);
-    }
-    return;
+  const bool in_box = dims.w != 0;
+  float4* vbox = reinterpret_cast<float4*>(smem);  // [vol]
+  if (in_box) {
+    velocity_box_async<GEOM>(L, lo, dims, vbox);
+    velocity_box_wait();
+    __syncthreads();
   }
-  float4* vbox = reinterpret_cast<float4*>(smem);               // [vol]
-  float4* rec = vbox + BOX_CELLS;                                // [XFER_GROUP_MAX]
-  Residues& R = *reinterpret_cast<Residues*>(rec + XFER_GROUP_MAX);
-  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
-  velocity_box_async<GEOM>(L, lo, dims, vbox);
-  __syncthreads();
-  // markers by residue of their first node's box index (-1: outside the box)
-  int li[XFER_PER_THREAD];
-#pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
-    li[q] = j < G.count ? box_index(m, G.first + j, lo, dims) : -1;
-    if (li[q] >= 0) atomicAdd(&R.cnt[li[q] & 31], 1);
-  }
-  __syncthreads();
-  residue_scan(R);
-  __syncthreads();
-  int pos[XFER_PER_THREAD];
-#pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    pos[q] = -1;
-    if (li[q] < 0) continue;
-    const int k = G.first + threadIdx.x + q * XFER_THREADS;
-    pos[q] = atomicAdd(&R.cur[li[q] & 31], 1);
-    rec[pos[q]] = make_float4(__int_as_float(li[q]), m.frac[k], m.frac[M + k], m.frac[2 * M + k]);
-  }
-  velocity_box_wait();
-  __syncthreads();
-  gather_records(vbox, dims, R, rec);
-  __syncthreads();
-  // results back in marker order: velocity, advection (FP64), stencil cache
-#pragma unroll
-  for (int q = 0; q < XFER_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
-    if (j >= G.count) continue;
+  for (int j = threadIdx.x; j < G.count; j += blockDim.x) {
     const int k = G.first + j;
+    Stencil st;
+    load_stencil(m, k, st);
+    double Xo[3] = {0.0, 0.0, 0.0};
+    if (moves)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Xo[a] = m.X[a * M + k];
+    const int ox = st.bx - lo.x, oy = st.by - lo.y, oz = st.bz - lo.z;
     float3 u;
-    if (pos[q] >= 0) {
-      const float4 r = rec[pos[q]];
-      u = make_float3(r.x, r.y, r.z);
-    } else {  // stencil outside the box
-      Stencil s;
-      load_stencil(m, k, s);
-      u = gather_global<GEOM>(L, s, false);
-    }
+    if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z)
+      u = box_gather(vbox, dims, st, ox, oy, oz);
+    else  // no box (every visited cell is cleared), or the stencil outside it
+      u = gather_global<GEOM>(L, st, !in_box);
     m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
-    if (moves) advect_marker(m, k, u.x, u.y, u.z);
+    if (moves) {
+      const float ua[3] = {u.x, u.y, u.z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double Xn = Xo[a] + (double)ua[a];
+        m.X[a * M + k] = Xn;
+        cache_coord(m, a * M + k, Xn);
+      }
+    }
+  }
+}
+
+
+// The stencil cache of one marker (first node and fractional offsets), as
+// read by the four lanes that share the marker.
+struct RawStencil {
+  int c[3];
+  float f[3];
+};
+__device__ __forceinline__ void load_raw(const MarkersDev& m, int k, RawStencil& r) {
+  const size_t M = (size_t)m.M;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    r.c[q] = m.cell[q * M + k];
+    r.f[q] = m.frac[q * M + k];
+  }
+}
+
+// Spreading of one marker group with four lanes per marker (launches of few
+// groups); the same fixed-point contributions as spread_group, so the same
+// sums. ibox: SPREAD_LANES_SMEM bytes.
+template <int GEOM>
+__device__ __forceinline__ void spread_group_lanes(const LatticeDev& L, const MarkersDev& m, const MarkerGroup G,
+                                                   int4* box_out, int* ibox) {
+  int4 lo, dims;
+  float fmax;
+  group_box(m, G, lo, dims, fmax);  // synchronises
+  if (threadIdx.x == 0) {
+    box_out[0] = lo;
+    box_out[1] = dims;
+  }
+  const bool any_force = fmax > 0.f;
+  const bool in_smem = dims.w != 0;
+  const int vol = dims.x * dims.y * dims.z;
+  const float S = any_force ? fminf(33554432.0f, 8589934592.0f / (float)G.count) / fmax : 0.f;  // as spread_group
+  if (in_smem) {
+    mark_box_tiles<GEOM>(L, lo, dims);
+    if (!any_force) return;
+    for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
+    __syncthreads();
+  }
+  const int a = threadIdx.x & 3;
+  const int per_pass = blockDim.x >> 2;
+  const int wfirst = (int)(threadIdx.x & ~31u) >> 2;  // first marker of this warp within a pass
+  // whole warps iterate together (shuffles in mark_tiles)
+  for (int j0 = 0; j0 + wfirst < G.count; j0 += per_pass) {
+    const int j = j0 + (int)(threadIdx.x >> 2);
+    const bool active = j < G.count;
+    const int k = G.first + (active ? j : 0);
+    RawStencil r;
+    load_raw(m, k, r);
+    const int bx = r.c[0] - 1, by = r.c[1] - 1, bz = r.c[2] - 1;
+    // the four lanes of a marker share its tiles: only the first stores them
+    if (!in_smem) mark_tiles<GEOM>(L, bx, by, bz, active);
+    if (!active || !any_force) continue;
+    const float wxa = axis_weight(r.f[0], a);
+    float wy[4], wz[4];
+    axis_weights(r.f[1], wy);
+    axis_weights(r.f[2], wz);
+    const float4 F = m.F[k];
+    if (in_smem) {
+      const float ax_ = F.x * S * wxa, ay_ = F.y * S * wxa, az_ = F.z * S * wxa;
+      int* p0 = ibox + (bx - lo.x + a) + dims.x * ((by - lo.y) + dims.y * (bz - lo.z));
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float wyz = wy[b] * wz[c];
+          int* p = p0 + dims.x * (b + dims.y * c);
+          atomicAdd(p, fixed_mul(ax_, wyz));
+          atomicAdd(p + vol, fixed_mul(ay_, wyz));
+          atomicAdd(p + 2 * vol, fixed_mul(az_, wyz));
+        }
+    } else {
+      const int x = wrapi(bx + a, L.nx);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int y = by + b, z = bz + c;
+          if (!fluid_row<GEOM>(L, y, z)) continue;
+          const float w = wxa * (wy[b] * wz[c]);
+          atomicAdd(L.g + (size_t)L.nx * (y + L.ny * z) + x, make_float4(F.x * w, F.y * w, F.z * w, 0.f));
+        }
+    }
+  }
+  if (!in_smem) return;
+  __syncthreads();
+  flush_box<GEOM>(L, lo, dims, ibox, 1.0f / S);
+}
+
+// Interpolation and advection of one marker group with four lanes per
+// marker (launches of few groups): lane a sums the stencil's x column a,
+// the four partial sums meet by shuffles, and lanes 0..2 advect one
+// coordinate each. The next pass's stencil cache is loaded before this
+// pass gathers. smem: INTERP_SMEM bytes (the velocity box).
+template <int GEOM>
+__device__ __forceinline__ void interpolate_group_lanes(const LatticeDev& L, const MarkersDev& m,
+                                                        const MarkerGroup G, const int4* box_in,
+                                                        unsigned char* smem) {
+  const int4 lo = box_in[0], dims = box_in[1];
+  const size_t M = (size_t)m.M;
+  const bool moves = !(G.flags & GROUP_FIXED);
+  const bool in_box = dims.w != 0;
+  float4* vbox = reinterpret_cast<float4*>(smem);  // [vol]
+  const int a = threadIdx.x & 3;
+  const int per_pass = blockDim.x >> 2;
+  const int slot = threadIdx.x >> 2;
+  const int wfirst = (int)(threadIdx.x & ~31u) >> 2;
+  if (in_box) velocity_box_async<GEOM>(L, lo, dims, vbox);
+  RawStencil nxt;
+  if (wfirst < G.count) load_raw(m, G.first + (slot < G.count ? slot : 0), nxt);
+  if (in_box) {
+    velocity_box_wait();
+    __syncthreads();
+  }
+  // whole warps iterate together (shuffles); a warp stops at the first pass
+  // that lies entirely past the group's end
+  for (int j0 = 0; j0 + wfirst < G.count; j0 += per_pass) {
+    const int j = j0 + slot;
+    const bool active = j < G.count;
+    const int k = G.first + (active ? j : 0);
+    const size_t off = (size_t)a * M + k;
+    double Xo = 0.0;
+    if (active && moves && a < 3) Xo = m.X[off];
+    const RawStencil cur = nxt;
+    if (j0 + per_pass + wfirst < G.count) {
+      const int jn = j + per_pass;
+      load_raw(m, G.first + (jn < G.count ? jn : 0), nxt);
+    }
+    const int bx = cur.c[0] - 1, by = cur.c[1] - 1, bz = cur.c[2] - 1;
+    const float wxa = axis_weight(cur.f[0], a);
+    float wy[4], wz[4];
+    axis_weights(cur.f[1], wy);
+    axis_weights(cur.f[2], wz);
+    const int ox = bx - lo.x, oy = by - lo.y, oz = bz - lo.z;
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z) {
+      const float4* p0 = vbox + (ox + a) + dims.x * (oy + dims.y * oz);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float4 v = p0[dims.x * (b + dims.y * c)];
+          const float wyz = wy[b] * wz[c];
+          ux = fmaf(wyz, v.x, ux);
+          uy = fmaf(wyz, v.y, uy);
+          uz = fmaf(wyz, v.z, uz);
+        }
+    } else {  // no box (every visited cell is cleared), or the stencil outside it
+      const int x = wrapi(bx + a, L.nx);
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int y = by + b, z = bz + c;
+          if (!fluid_row<GEOM>(L, y, z)) continue;
+          const size_t gi = (size_t)L.nx * (y + L.ny * z) + x;
+          const float4 v = L.uw[gi];
+          if (!in_box) L.g[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float wyz = wy[b] * wz[c];
+          ux = fmaf(wyz, v.x, ux);
+          uy = fmaf(wyz, v.y, uy);
+          uz = fmaf(wyz, v.z, uz);
+        }
+    }
+    ux *= wxa;
+    uy *= wxa;
+    uz *= wxa;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      ux += __shfl_xor_sync(0xffffffffu, ux, o);
+      uy += __shfl_xor_sync(0xffffffffu, uy, o);
+      uz += __shfl_xor_sync(0xffffffffu, uz, o);
+    }
+    if (!active) continue;
+    if (a == 0) m.U[k] = make_float4(ux, uy, uz, 0.f);
+    if (a < 3 && moves) {
+      const double Xn = Xo + (double)(a == 0 ? ux : (a == 1 ? uy : uz));
+      m.X[off] = Xn;
+      cache_coord(m, off, Xn);
+    }
   }
 }
 

@@ -81,3 +81,26 @@ def wide_tracers(lat, M, seed):
         X = np.stack([nx * rng.random(M), (ny - 1) * rng.random(M), nz * rng.random(M)])
     F = 2e-3 * (2 * rng.random((3, M)) - 1)
     return X, F
+
+
+
+def cluster_tracers(lat, n_clusters, seed, per=256, half=2.5):
+    """Tracers in runs of `per` (one transfer group each) packed into cubes
+    of side 2 * half around random centres in the fluid, so that every
+    group's stencils fit a shared-memory box; the last run is ragged. Some
+    clusters sit across periodic boundaries and within 2 lu of walls."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape(lat)
+    n = n_clusters
+    if lat['geometry'] == 2:
+        r = (lat["tube_radius"] - 1.5 * half - 0.5) * np.sqrt(rng.random(n))
+        th = 2 * np.pi * rng.random(n)
+        C = np.stack([nx * rng.random(n), (ny - 1) / 2 + r * np.cos(th), (nz - 1) / 2 + r * np.sin(th)])
+    else:
+        C = np.stack([nx * rng.random(n), half + (ny - 1 - 2 * half) * rng.random(n), nz * rng.random(n)])
+        if lat['geometry'] == 0:
+            C[1] = ny * rng.random(n)
+    X = np.repeat(C, per, axis=1) + rng.uniform(-half, half, (3, n * per))
+    X = X[:, : n * per - per // 3]
+    F = 2e-3 * (2 * rng.random(X.shape) - 1)
+    return X, F

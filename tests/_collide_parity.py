@@ -52,42 +52,9 @@ def check_collide_parity(binding, lat, steps=3, seed=11, tol=2e-7, markers=None)
     return worst
 
 
-def run_stages(binding, lat, storage, steps, seed, markers):
-    """Random populations, then `steps` of spread, collide, interpolate with
-    fixed tracer forces; returns the populations (FP64, natural layout)."""
-    sim = binding.Simulation(lat, storage=storage)
-    fl = fluid_mask(lat)
-    f0 = I.random_populations(shape(lat), seed, amp=0.02)
-    f0[:, ~fl] = 0.0
-    sim.set_populations(f0)
-    X, F = markers
-    sim.set_markers(None, [], X)
-    sim.set_marker_forces(F)
-    for _ in range(steps):
-        sim.stage(binding.STAGE_SPREAD)
-        sim.stage(binding.STAGE_COLLIDE)
-        sim.stage(binding.STAGE_INTERP)
-    f = sim.populations()
-    rho, u = sim.fields()
-    sim.close()
-    return f, rho, u
-
-
 def main():
-    import sys
     from paper_1704_04551_gb300 import binding
     binding.load()
-    if len(sys.argv) > 1 and sys.argv[1] == 'dump':
-        # python -m tests._collide_parity dump STORAGE OUT.npz: the WIDE
-        # lattices through this build, three steps each
-        from tests._cases import WIDE, wide_tracers
-        out = {}
-        for geom, lat in WIDE.items():
-            f, rho, u = run_stages(binding, lat, sys.argv[2], 3, 17, wide_tracers(lat, 2000, 18))
-            out[geom + '_f'], out[geom + '_rho'], out[geom + '_u'] = f, rho, u
-        np.savez(sys.argv[3], **out)
-        print('dumped', len(out))
-        return
     for geom, lat in LATTICES.items():
         err = check_collide_parity(binding, lat)
         print(f'{geom} ok {err:.3e}')

@@ -10,8 +10,11 @@ against the FP64 oracle through the C ABI:
 * the membrane force scatter in fixed point (taken once a previous step set
   the body's scale) and its float redo (taken when a contribution outgrows
   that scale) (Sec. 2.2, Eqs. membrane-potential .. volumeEnergy);
-* the two-cells-per-thread collide of the half-precision formats, bit for
-  bit against a build that keeps one cell per thread (IBM_HALF_PER_CELL);
+* both families of transfer kernels: launches of fewer than 512 marker
+  groups take four lanes per marker in large blocks, launches of more take
+  one thread per marker with bank-sorted shared-memory atomics; spreading
+  and interpolation with shared-memory boxes, through each family
+  (Sec. 2.3, Eqs. ibmForceSpread, ibmVelocityInterpret);
 * the fused coupling kernel of membrane suspensions (interpolation, forces
   and spreading per body between two collisions, two force-density
   buffers), which ibm_lbm_step takes for chunks of 16 and 64 steps, against
@@ -27,7 +30,7 @@ import pytest
 
 import oracle as O
 from paper_1704_04551_gb300 import inputs as I
-from tests._cases import WIDE, membrane_case, shape, wide_tracers
+from tests._cases import WIDE, cluster_tracers, membrane_case, shape, wide_tracers
 from tests._collide_parity import check_collide_parity
 
 pytestmark = pytest.mark.gpu
@@ -54,29 +57,34 @@ def test_collide_64bit_offsets_variant(cuda_lib):
     assert r.stdout.count(' ok ') == 3, r.stdout
 
 
-@pytest.mark.parametrize('storage', ['f16', 'bf16'])
-def test_half_pair_collide_bitwise_equal_to_one_cell(cuda_lib, storage, tmp_path):
-    """The paired half-precision collide does the one-cell arithmetic and
-    stores the same 16-bit values: populations, densities and velocities
-    after three coupled stages on the wide lattices (rows of 160 cells: full
-    and partial warps, the periodic wrap of x, warp-edge half stores) equal
-    those of the one-cell build exactly."""
-    from paper_1704_04551_gb300 import build
-    from tests._collide_parity import run_stages
-    out = os.path.join(build.BUILD, 'halfcell', 'libibmlbm.so')
-    os.makedirs(os.path.dirname(out), exist_ok=True)
-    build.build(extra=['-DIBM_HALF_PER_CELL'], out=out)
-    dump = str(tmp_path / 'onecell.npz')
-    env = dict(os.environ, IBM_LBM_LIBRARY=out, PYTHONPATH=ROOT + os.pathsep + os.environ.get('PYTHONPATH', ''))
-    r = subprocess.run([sys.executable, '-m', 'tests._collide_parity', 'dump', storage, dump], cwd=ROOT, env=env,
-                       capture_output=True, text=True, timeout=900)
-    assert r.returncode == 0, r.stdout + r.stderr
-    ref = np.load(dump)
-    for geom, lat in WIDE.items():
-        f, rho, u = run_stages(cuda_lib, lat, storage, 3, 17, wide_tracers(lat, 2000, 18))
-        assert np.array_equal(f, ref[geom + '_f']), geom
-        assert np.array_equal(rho, ref[geom + '_rho']), geom
-        assert np.array_equal(u, ref[geom + '_u']), geom
+@pytest.mark.parametrize('n_clusters', [40, 600])
+@pytest.mark.parametrize('geom', list(WIDE))
+def test_transfer_kernel_families(cuda_lib, geom, n_clusters):
+    """Spreading, then interpolation and advection through the boxes the
+    spreading computed, for 40 groups (four-lanes kernels) and 600 groups
+    (sorted kernels), against the oracle."""
+    from paper_1704_04551_gb300.binding import Simulation
+    lat = WIDE[geom]
+    X, F = cluster_tracers(lat, n_clusters, 31 + n_clusters)
+    sim, ora = Simulation(lat), O.Oracle(lat)
+    sim.set_markers(None, [], X)
+    ora.set_bodies([], X)
+    sim.set_marker_forces(F)
+    ora.set_marker_forces(F)
+    sim.stage(cuda_lib.STAGE_SPREAD)
+    ora.stage_spread()
+    gg, go = sim.force_density(), ora.force_density()
+    assert np.abs(gg - go).max() < 2e-5 * np.abs(go).max()
+    assert np.allclose(gg.sum(1), go.sum(1), rtol=1e-5, atol=1e-9)
+    rho, u = I.random_fields(shape(lat), 32)
+    sim.set_lattice(rho, u)
+    ora.set_equilibrium(rho, u)
+    sim.stage(cuda_lib.STAGE_INTERP)
+    ora.stage_interpolate()
+    Xg, Ug, _ = sim.markers()
+    Xo, Uo, _ = ora.markers()
+    assert np.abs(Ug - Uo).max() < 2e-5 * np.abs(Uo).max()
+    assert np.abs(Xg - Xo).max() < 1e-6
 
 
 def test_membrane_forces_fixed_point_after_steps(cuda_lib):
