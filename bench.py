@@ -212,6 +212,35 @@ def collide_source_sha():
     return h.hexdigest()[:16]
 
 
+def couple_source_sha():
+    """Hash of the sources the fused coupling kernel is built from."""
+    h = hashlib.sha256()
+    for name in ('common.cuh', 'transfer_group.cuh', 'forces_body.cuh', 'couple.cu'):
+        with open(os.path.join(ROOT, 'paper_1704_04551_gb300', 'csrc', name), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def couple_traffic(bodies):
+    """DRAM bytes per fused coupling launch: the committed ncu summary's
+    bytes per body times the bodies, if the kernel source is unchanged since
+    the capture."""
+    p = os.path.join(ROOT, 'profiles', 'couple_tube160_f32.md')
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ':' in line and line.startswith('- '):
+            k, v = line[2:].split(':', 1)
+            vals[k.strip()] = v.strip().strip('`')
+    if vals.get('couple source sha256 prefix') != couple_source_sha():
+        return None
+    try:
+        return float(vals['dram bytes per body']) * bodies
+    except (KeyError, ValueError):
+        return None
+
+
 def collide_traffic(storage):
     """DRAM bytes per collide launch from the committed ncu summary, if the
     kernel source is unchanged since it was taken."""
@@ -394,7 +423,8 @@ def fused_path(w, storage):
         return False
     if any(b['kind'] != 0 for b in bodies):
         return False
-    return sum(b['count'] for b in bodies) == w['X'].shape[1] and w['mesh']['rest_X'].shape[1] <= 1024
+    # templates of up to 704 vertices (two per thread of the fused kernel)
+    return sum(b['count'] for b in bodies) == w['X'].shape[1] and w['mesh']['rest_X'].shape[1] <= 704
 
 
 def run_ours(args):
@@ -448,28 +478,57 @@ def run_ours(args):
     stages = sim.timing()
     sim.set_timing(0)
     value = aggregate(N * args.steps, ms_max / 1e3, ws) / 1e6
+    # the same K steps on the production path with events around the
+    # collision and the fused coupling kernel of every step that launches it
+    # (membrane suspensions; other handles report per-stage times here)
+    fused = fused_path(w, storage)
+    prod = None
+    if fused:
+        sim.set_timing(args.steps, fused=True)
+        sim.step(args.steps)
+        prod = sim.timing()
+        sim.set_timing(0)
+        if not (prod['steps'] > 0 and prod['forces_ms'] == 0.0 and prod['spread_ms'] == 0.0):
+            fused, prod = False, None
 
-    # ---- roofline of the collide-stream kernel and of the whole step --------
-    # (the collide kernel is the same in the separate-kernel and the fused
-    # path; its duration comes from the event-per-stage run)
+    # ---- rooflines: the collide-stream kernel, the fused coupling kernel and
+    # the whole step. Algorithmic bytes per unit: N_f*38*s_p + N_touch*24 for
+    # the collision (populations read and written once; force density read
+    # and velocity written on touched cells), M*72 for the coupling (FP64 X
+    # read and written, FP32 U and F handed off per marker). Launch durations
+    # from CUDA events on the library's stream: the production-path timing
+    # run for membrane suspensions, the per-stage run otherwise.
     sp = bytes_per_pop(storage)
     n_touch = touched_cells(lat, w['X'])
     alg_bytes = Nf * 38 * sp + n_touch * 24
-    collide_s = stages['collide_ms'] / 1e3 / max(1, stages['steps'])
+    t = prod if prod is not None else stages
+    collide_s = t['collide_ms'] / 1e3 / max(1, t['steps'])
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / collide_s / 1e9
     step_alg = alg_bytes + M * 72
     step_s = ms_max / 1e3 / args.steps
-    roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
-                traffic=collide_traffic(storage), kernel='k_collide (fused collide-stream-force)',
-                peak_source=f'{peak_kind} hbm_gbs (burst copy)',
-                alg_bytes_per_launch=alg_bytes, step_alg_bytes=step_alg,
+    collide = dict(kernel='k_collide (fused collide-stream-force)', bound='hbm', achieved=achieved, peak=peak,
+                   unit='GB/s', frac=achieved / peak, traffic=collide_traffic(storage),
+                   alg_bytes_per_launch=alg_bytes, launch_ms=collide_s * 1e3)
+    step = dict(step_alg_bytes=step_alg,
                 step_alg_bytes_formula='N_f*38*s_p + N_touch*24 + M*72 (populations read+written once, force '
                                        'density read and velocity written on touched cells, FP64 X read+written '
                                        'and FP32 U, F per marker)',
                 step_achieved=step_alg / step_s / 1e9,
                 step_frac=(step_alg / step_s / 1e9) / peak)
-    fused = fused_path(w, storage)
+    if prod is not None:
+        # the fused coupling kernel takes the larger share of the step
+        couple_s = prod['interp_ms'] / 1e3 / prod['steps']
+        c_bytes = M * 72
+        c_ach = c_bytes / couple_s / 1e9
+        roof = dict(bound='hbm', achieved=c_ach, peak=peak, unit='GB/s', frac=c_ach / peak,
+                    traffic=couple_traffic(len(w['bodies'])),
+                    kernel='k_couple (fused: interpolation + advection, membrane forces, spreading of the next step)',
+                    alg_bytes_per_launch=c_bytes, alg_bytes_formula='M*72', launch_ms=couple_s * 1e3,
+                    note='latency-bound (see profiles/couple_tube160_f32.md); the HBM-bound kernel is `collide`',
+                    peak_source=f'{peak_kind} hbm_gbs (burst copy)', collide=collide, **step)
+    else:
+        roof = dict(collide, peak_source=f'{peak_kind} hbm_gbs (burst copy)', **step)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     rho0 = np.ones(N)
@@ -526,6 +585,10 @@ def run_ours(args):
                         production_path='collide + fused coupling kernel per step (membrane suspension)' if fused
                         else 'separate kernels per stage',
                         coupling_ms_per_step=ms_max / args.steps - split['collide_ms'],
+                        production_ms_per_launch=None if prod is None else dict(
+                            collide_ms=prod['collide_ms'] / prod['steps'], couple_ms=prod['interp_ms'] / prod['steps'],
+                            steps_timed=prod['steps'],
+                            note='events around each collision and each fused coupling kernel, direct launches'),
                         staged_path_ms_per_step=staged_ms / args.steps,
                         stage_ms_per_step=split,
                         coupling_share=(split['spread_ms'] + split['interp_ms']) / max(1e-12, tot / max(1, stages['steps'])),

@@ -247,6 +247,19 @@ int ibm_lbm_get_force_density(ibm_lbm_t* h, double* g);
  * odd (neighbour-addressed) AA steps; then resets the sums. */
 int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps);
 int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]);
+/* Timing of the production path of membrane suspensions. With on != 0 and
+ * timing on, a handle that takes the fused coupling kernel (see
+ * ibm_lbm_step) runs its timed steps on that path, with direct launches:
+ * each step that launches the fused kernel is timed, out[2] receiving its
+ * collision and out[3] the fused kernel (interpolation and advection of the
+ * step, marker forces and spreading of the next, Sec. 2.3) with the clear
+ * of the touched-tile flags before it; out[0] and out[1] stay zero and
+ * out[4] counts these steps. The other steps of the call (the first step's
+ * forces and spreading, a step that restores the even AA parity, the last
+ * step) run untimed. A handle that does not take the fused path is timed
+ * stage by stage as above. on = 0 (the default) restores that for every
+ * handle. Returns E_ARG for a NULL handle. */
+int ibm_lbm_set_timing_fused(ibm_lbm_t* h, int on);
 
 /* ---------------------------------------------------------------------------
  * Serving: many independent simulations on one GPU with continuous batching.

@@ -105,6 +105,7 @@ def load():
         'ibm_lbm_get_force_density': ([P, P], C.c_int),
         'ibm_lbm_set_timing': ([P, I64], C.c_int),
         'ibm_lbm_get_timing': ([P, P], C.c_int),
+        'ibm_lbm_set_timing_fused': ([P, I32], C.c_int),
         'ibm_lbm_spread_noalloc': ([P, P, I64, I32, I32, I32, I32, D, P, P], C.c_int),
         'ibm_lbm_stream': ([P], P),
         'ibm_lbm_device_bytes': ([P], C.c_size_t),
@@ -254,6 +255,10 @@ def ibm_lbm_get_force_density(h, g):
 
 def ibm_lbm_set_timing(h, max_steps):
     return _check(h, load().ibm_lbm_set_timing(h, int(max_steps)))
+
+
+def ibm_lbm_set_timing_fused(h, on):
+    return _check(h, load().ibm_lbm_set_timing_fused(h, 1 if on else 0))
 
 
 def ibm_lbm_get_timing(h):
@@ -531,8 +536,9 @@ class Simulation:
     def stage(self, stage):
         ibm_lbm_run_stage(self.h, stage)
 
-    def set_timing(self, max_steps):
+    def set_timing(self, max_steps, fused=False):
         ibm_lbm_set_timing(self.h, max_steps)
+        ibm_lbm_set_timing_fused(self.h, fused)
 
     def timing(self):
         t = ibm_lbm_get_timing(self.h)

@@ -196,6 +196,7 @@ void enqueue_timed_step(ibm_lbm_t* h, bool odd, bool dense) {
   mark(4);
   if (rec) {
     h->timed_odd.push_back(odd ? 1 : 0);
+    h->timed_fused.push_back(0);
     h->timed_steps++;
   }
 }
@@ -223,10 +224,15 @@ int capture(ibm_lbm_t* h, cudaGraphExec_t* out, int n, bool odd0, bool dense_las
 // the other buffer; the last step's interpolation runs alone. The tile flags
 // are cleared between a collision and the spreading that follows it.
 bool fused_applies(const ibm_lbm_t* h) {
-  return h->n_couple > 0 && !h->timing && !(h->morse_rc > 0.0) && h->gbuf2 != nullptr;
+  return h->n_couple > 0 && (!h->timing || h->timing_fused) && !(h->morse_rc > 0.0) && h->gbuf2 != nullptr;
 }
 
-void enqueue_fused_chunk(ibm_lbm_t* h, int n) {
+// With timed, the steps that launch the fused kernel record the events
+// around the collision and around the tile-flag clear and the fused kernel
+// (the forces and spreading slots of such a step are not read); the first
+// step's forces and spreading and the last step's interpolation lie outside
+// the timed intervals.
+void enqueue_fused_chunk(ibm_lbm_t* h, int n, bool timed) {
   cudaStream_t st = h->stream;
   LatticeDev L0 = h->L;
   L0.g = h->gbuf;
@@ -234,9 +240,16 @@ void enqueue_fused_chunk(ibm_lbm_t* h, int n) {
   enqueue_forces(h, st);
   launch_spread(L0, h->m, h->groups, h->n_groups, h->boxes, st);
   for (int s = 0; s < n; ++s) {
+    const size_t base = 5 * h->timed_steps;
+    const bool rec = timed && s + 1 < n && base + 5 <= h->events.size();
+    auto mark = [&](int k) {
+      if (rec) cudaEventRecord(h->events[base + k], st);
+    };
     LatticeDev Ls = h->L;
     Ls.g = (s & 1) ? h->gbuf2 : h->gbuf;
+    mark(2);
     launch_collide(Ls, h->rows, h->n_rows, h->cfg.storage, (s & 1) != 0, false, st);
+    mark(3);
     if (s + 1 < n) {
       cudaMemsetAsync(Ls.flags, 0, (size_t)tiles(Ls), st);
       launch_couple(Ls, (s & 1) ? h->gbuf : h->gbuf2, h->m, h->d_bodies, h->couple_items, h->n_couple, h->groups,
@@ -244,13 +257,19 @@ void enqueue_fused_chunk(ibm_lbm_t* h, int n) {
     } else {
       launch_interpolate(Ls, h->m, h->groups, h->n_groups, h->boxes, st);
     }
+    mark(4);
+    if (rec) {
+      h->timed_odd.push_back((s & 1) ? 1 : 0);
+      h->timed_fused.push_back(1);
+      h->timed_steps++;
+    }
   }
 }
 
 int capture_fused(ibm_lbm_t* h, cudaGraphExec_t* out, int n) {
   cudaGraph_t g = nullptr;
   CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_fused_chunk(h, n);
+  enqueue_fused_chunk(h, n, false);
   CUDA_TRY(h, cudaStreamEndCapture(h->stream, &g));
   cudaError_t e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
@@ -291,19 +310,34 @@ int enqueue_steps(ibm_lbm_t* h, int64_t n) {
   if (n == 0) return IBM_LBM_OK;
   h->boxes_valid = false;  // the last interpolation moves the markers
   int64_t left = n;
+  if (h->n_couple > 0 && !h->gbuf2 && (h->timing ? h->timing_fused && left > 2 : left > CHUNK)) {
+    // second force-density buffer of the fused path, zero like the first
+    h->gbuf2 = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * (size_t)h->L.N);
+    if (h->gbuf2) CUDA_TRY(h, cudaMemsetAsync(h->gbuf2, 0, sizeof(float4) * (size_t)h->L.N, h->stream));
+  }
   if (h->timing) {
-    for (; left > 0; --left) {
-      enqueue_timed_step(h, h->odd_next, left == 1);
+    // with timing_fused, a handle on the fused path times only its fused
+    // steps; every other handle is timed stage by stage
+    const bool fused = h->timing_fused && fused_applies(h);
+    while (left > 0) {
+      if (fused && !h->odd_next && left > 2) {
+        // the fused path with direct launches; the last step stays separate
+        // (it writes the velocity of every cell)
+        const int m = (int)std::min<int64_t>(left - 1, 1 << 22);
+        enqueue_fused_chunk(h, m, true);
+        left -= m;
+        h->steps += m;
+        if (m & 1) h->odd_next = !h->odd_next;
+        continue;
+      }
+      if (fused) enqueue_step(h, h->odd_next, left == 1);
+      else enqueue_timed_step(h, h->odd_next, left == 1);
+      --left;
       h->steps += 1;
       h->odd_next = !h->odd_next;
     }
     CUDA_TRY(h, cudaGetLastError());
     return enqueue_diagnostics(h);
-  }
-  if (h->n_couple > 0 && !h->gbuf2 && !h->timing && left > CHUNK) {
-    // second force-density buffer of the fused path, zero like the first
-    h->gbuf2 = (float4*)dalloc(h, h->lattice_mem, sizeof(float4) * (size_t)h->L.N);
-    if (h->gbuf2) CUDA_TRY(h, cudaMemsetAsync(h->gbuf2, 0, sizeof(float4) * (size_t)h->L.N, h->stream));
   }
   while (left > 0) {
     if (fused_applies(h) && !h->odd_next && left > CHUNK) {
@@ -1320,6 +1354,7 @@ static int impl_ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   h->events.clear();
   h->timed_steps = 0;
   h->timed_odd.clear();
+  h->timed_fused.clear();
   h->timing = max_steps > 0;
   for (int64_t i = 0; i < 5 * max_steps; ++i) {
     cudaEvent_t e;
@@ -1329,12 +1364,18 @@ static int impl_ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   return IBM_LBM_OK;
 }
 
+static int impl_ibm_lbm_set_timing_fused(ibm_lbm_t* h, int on) {
+  if (!h) return IBM_LBM_E_ARG;
+  h->timing_fused = on != 0;
+  return IBM_LBM_OK;
+}
+
 static int impl_ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
   if (!h || !out) return IBM_LBM_E_ARG;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < 6; ++k) out[k] = 0.0;
   for (size_t s = 0; s < h->timed_steps; ++s)
-    for (int k = 0; k < 4; ++k) {
+    for (int k = h->timed_fused[s] ? 2 : 0; k < 4; ++k) {
       float ms = 0.f;
       CUDA_TRY(h, cudaEventElapsedTime(&ms, h->events[5 * s + k], h->events[5 * s + k + 1]));
       out[k] += ms;
@@ -1343,6 +1384,7 @@ static int impl_ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {
   out[4] = (double)h->timed_steps;
   h->timed_steps = 0;
   h->timed_odd.clear();
+  h->timed_fused.clear();
   return IBM_LBM_OK;
 }
 
@@ -1437,6 +1479,10 @@ int ibm_lbm_get_bodies(ibm_lbm_t* h, ibm_lbm_body* bodies, int32_t n_bodies) {
 
 int ibm_lbm_set_timing(ibm_lbm_t* h, int64_t max_steps) {
   return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_timing(h, max_steps); });
+}
+
+int ibm_lbm_set_timing_fused(ibm_lbm_t* h, int on) {
+  return abi_guard(h, [&]() -> int { return impl_ibm_lbm_set_timing_fused(h, on); });
 }
 
 int ibm_lbm_get_timing(ibm_lbm_t* h, double out[6]) {

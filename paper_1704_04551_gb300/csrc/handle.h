@@ -84,8 +84,10 @@ struct ibm_lbm {
   // per-stage timing (events between stages, direct launches)
   std::vector<cudaEvent_t> events;  // 5 per timed step
   std::vector<char> timed_odd;      // AA parity of each timed step
+  std::vector<char> timed_fused;    // timed step on the fused path (no forces / spreading slots)
   size_t timed_steps = 0;
   bool timing = false;
+  bool timing_fused = false;  // time the fused path where it applies
   // graphs
   cudaGraphExec_t g_chunk = nullptr;
   cudaGraphExec_t g_fused[2] = {nullptr, nullptr};  // fused chunks of FUSED_LONG and CHUNK steps

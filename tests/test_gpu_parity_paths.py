@@ -159,3 +159,38 @@ def test_fused_membrane_chunks_match_stages_and_oracle(cuda_lib):
     assert rel_l2(ua[:, fl], uo[:, fl]) < 1e-5
     assert np.abs(Xa - Xo).max() < 1e-5
     assert np.abs(Fa - Fo).max() < 1e-3 * np.abs(Fo).max()
+
+
+def test_fused_path_timing_mode(cuda_lib):
+    """ibm_lbm_set_timing_fused: a membrane suspension times its fused steps
+    (starting at an even AA step, all but the last of the call's steps, the
+    last one separate): forces and spreading slots zero, collisions and fused
+    kernels timed; the results equal those of the graph path to rounding. A
+    handle with tracers only is still timed stage by stage."""
+    w = membrane_case()
+    w['lattice'] = dict(w['lattice'], body_force=[2e-6, 0, 0])
+    steps = 20
+    a = cuda_lib.Simulation.from_workload(w)
+    a.step(steps)
+    b = cuda_lib.Simulation.from_workload(w)
+    b.set_timing(steps, fused=True)
+    b.step(steps)
+    t = b.timing()
+    b.set_timing(0)
+    assert t['steps'] == steps - 2
+    assert t['forces_ms'] == 0.0 and t['spread_ms'] == 0.0
+    assert t['collide_ms'] > 0.0 and t['interp_ms'] > 0.0
+    from tests._cases import fluid_mask, rel_l2
+    fl = fluid_mask(w['lattice'])
+    assert rel_l2(a.fields()[1][:, fl], b.fields()[1][:, fl]) < 1e-6
+    assert np.abs(a.markers()[0] - b.markers()[0]).max() < 1e-7
+    assert b.diagnostics()['steps'] == steps
+    lat = WIDE['periodic']
+    X, F = wide_tracers(lat, 500, 3)
+    c = cuda_lib.Simulation(lat)
+    c.set_markers(None, [], X)
+    c.set_timing(4, fused=True)
+    c.step(4)
+    tc = c.timing()
+    assert tc['steps'] == 4 and tc['spread_ms'] > 0.0
+
