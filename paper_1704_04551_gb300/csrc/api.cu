@@ -253,7 +253,7 @@ void enqueue_fused_chunk(ibm_lbm_t* h, int n, bool timed) {
     if (s + 1 < n) {
       cudaMemsetAsync(Ls.flags, 0, (size_t)tiles(Ls), st);
       launch_couple(Ls, (s & 1) ? h->gbuf : h->gbuf2, h->m, h->d_bodies, h->couple_items, h->n_couple, h->groups,
-                    h->boxes, h->mesh, st);
+                    h->boxes, h->couple_order, h->mesh, st);
     } else {
       launch_interpolate(Ls, h->m, h->groups, h->n_groups, h->boxes, st);
     }
@@ -868,6 +868,7 @@ static void clear_markers(ibm_lbm_t* h) {
   h->boxes = nullptr;
   h->couple_items = nullptr;
   h->n_couple = 0;
+  h->couple_order = nullptr;
   h->need_zero_F = false;
 }
 
@@ -1106,6 +1107,8 @@ static int set_markers_into(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bo
       }
       if (fused && (int)items.size() == n_bodies) {
         if ((rc = upload<int2>(h, h->marker_mem, &h->couple_items, items.data(), items.size()))) return rc;
+        h->couple_order = (unsigned char*)dalloc(h, h->marker_mem, couple_order_bytes(h->mesh) * items.size());
+        if (!h->couple_order) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");
         h->n_couple = (int)items.size();
       }
     }

@@ -40,6 +40,16 @@ __host__ __device__ constexpr int couple_residues_offset(int nv, int nt) {
   return (most + 15) / 16 * 16;
 }
 
+// Part 1 keeps, after the velocity box, the gathered velocities [nv]
+// float4 and the gather order [nv] ushort.
+__host__ __device__ constexpr int couple_gather_end(int nv) { return BOX_CELLS * 16 + 18 * nv; }
+
+// Per-body record the spreading leaves for the next step's gather: the
+// residue counters (counts [32], starts [32], largest count) of the
+// vertices' first stencil nodes in the box it wrote, then the vertex order.
+constexpr int ORDER_META_INTS = 68;
+__host__ __device__ constexpr int couple_order_stride(int nv) { return (ORDER_META_INTS * 4 + 2 * nv + 15) / 16 * 16; }
+
 namespace {
 
 // Stencil of vertex v from the positions in shared memory (integer parts
@@ -55,59 +65,72 @@ __device__ __forceinline__ void smem_cell(const MembraneSmem& S, int nv, int v, 
 
 template <int GEOM>
 __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* B,
-                                                const MarkerGroup G, int4* box, const MeshDev& mesh,
-                                                unsigned char* smem, double* red) {
+                                                const MarkerGroup G, int4* box, unsigned char* orec,
+                                                const MeshDev& mesh, unsigned char* smem, double* red) {
   __shared__ int s_lo[3], s_hi[3];
   __shared__ unsigned s_fmax;
   const size_t M = (size_t)m.M;
   const int nv = mesh.nv, nt = mesh.nt;  // G.count == nv
   const int4 lo = box[0], dims = box[1];
   const bool in_box = dims.w != 0;
+  // lo.w != 0: the previous step's spreading left the residue order of
+  // these stencils in this box (orec)
+  const bool ordered = in_box && lo.w != 0;
   float4* vbox = reinterpret_cast<float4*>(smem);
+  float4* uS = reinterpret_cast<float4*>(smem + BOX_CELLS * 16);         // [nv] gathered velocities
+  unsigned short* oS = reinterpret_cast<unsigned short*>(uS + nv);        // [nv] gather order
+  const int* ometa = reinterpret_cast<const int*>(orec);
+  const unsigned short* oidx = reinterpret_cast<const unsigned short*>(orec + ORDER_META_INTS * 4);
   Residues& R = *reinterpret_cast<Residues*>(smem + couple_residues_offset(nv, nt));
   // origin of the integer parts in shared memory: the first vertex's cell
   // before this step's advection (read before any thread writes the cache)
   const int3 o = make_int3(m.cell[G.first], m.cell[M + G.first], m.cell[2 * M + G.first]);
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
 
   // ---- 1. interpolation of step n and advection --------------------------
-  // Each thread gathers for its own markers: the bank conflicts of the
-  // gather cost less here than the extra passes and barriers of sorting the
-  // markers by residue (measured); the new stencil of each marker is kept in
-  // registers until the velocity box, which the positions overwrite, is done.
-  if (in_box) {
-    velocity_box_async<GEOM>(L, lo, dims, vbox);
-    velocity_box_wait();
-    __syncthreads();
-  }
-  int cnew[COUPLE_PER_THREAD][3];
-  float fnew[COUPLE_PER_THREAD][3];
+  // The velocity box loads while the block reads its markers' FP64
+  // positions and the gather order. With the order, lane r of a warp gathers
+  // for the markers whose first node has box index = r (mod 32), so that
+  // the 16-byte loads of a quarter warp fall in distinct banks; without it
+  // (the first step after separate kernels) each thread gathers for its own
+  // markers. The velocities go to shared memory; after a barrier each thread
+  // advects its own markers and writes their positions over the box.
+  if (in_box) velocity_box_async<GEOM>(L, lo, dims, vbox);
+  double Xo[COUPLE_PER_THREAD][3];
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
     const int j = threadIdx.x + q * XFER_THREADS;
-    if (j >= G.count) continue;
-    const int k = G.first + j;
-    Stencil st;
-    load_stencil(m, k, st);
-    double Xo[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Xo[a] = m.X[a * M + k];
+    for (int a = 0; a < 3; ++a) Xo[q][a] = j < nv ? m.X[a * M + G.first + j] : 0.0;
+  }
+  int ocnt = 0, ost = 0, omost = 0;
+  if (ordered) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) oS[i] = oidx[i];
+    ocnt = ometa[lane];
+    ost = ometa[32 + lane];
+    omost = ometa[64];
+  }
+  if (in_box) velocity_box_wait();
+  __syncthreads();
+  auto gather = [&](int j) {
+    Stencil st;
+    load_stencil(m, G.first + j, st);
     const int ox = st.bx - lo.x, oy = st.by - lo.y, oz = st.bz - lo.z;
     float3 u;
     if (in_box && ox >= 0 && oy >= 0 && oz >= 0 && ox + 4 <= dims.x && oy + 4 <= dims.y && oz + 4 <= dims.z)
       u = box_gather(vbox, dims, st, ox, oy, oz);
     else  // no box, or the stencil outside it
       u = gather_global<GEOM>(L, st, !in_box);
-    m.U[k] = make_float4(u.x, u.y, u.z, 0.f);
-    const float ua[3] = {u.x, u.y, u.z};
+    uS[j] = make_float4(u.x, u.y, u.z, 0.f);
+  };
+  if (ordered) {
+    for (int w = threadIdx.x >> 5; w < omost; w += nwarps)
+      if (w < ocnt) gather(oS[ost + w]);
+  } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double Xn = Xo[a] + (double)ua[a];
-      m.X[a * M + k] = Xn;
-      const double fl = floor(Xn);
-      cnew[q][a] = (int)fl;
-      fnew[q][a] = (float)(Xn - fl);
-      m.cell[a * M + k] = cnew[q][a];
-      m.frac[a * M + k] = fnew[q][a];
+    for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
+      const int j = threadIdx.x + q * XFER_THREADS;
+      if (j < nv) gather(j);
     }
   }
   __syncthreads();  // the velocity box is done: the positions go over it
@@ -116,11 +139,22 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
     const int j = threadIdx.x + q * XFER_THREADS;
-    if (j >= G.count) continue;
+    if (j >= nv) continue;
+    const int k = G.first + j;
+    const float4 u = uS[j];
+    m.U[k] = u;
+    const float ua[3] = {u.x, u.y, u.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      S.sI[a * nv + j] = (float)(cnew[q][a] - oa[a]);
-      S.sR[a * nv + j] = fnew[q][a];
+      const double Xn = Xo[q][a] + (double)ua[a];
+      m.X[a * M + k] = Xn;
+      const double fl = floor(Xn);
+      const int c = (int)fl;
+      const float f = (float)(Xn - fl);
+      m.cell[a * M + k] = c;
+      m.frac[a * M + k] = f;
+      S.sI[a * nv + j] = (float)(c - oa[a]);
+      S.sR[a * nv + j] = f;
     }
   }
   __syncthreads();
@@ -174,10 +208,11 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   __syncthreads();
   const long long ex = (long long)s_hi[0] - s_lo[0] + 4, ey = (long long)s_hi[1] - s_lo[1] + 4,
                   ez = (long long)s_hi[2] - s_lo[2] + 4;
-  const int4 lo2 = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, 0);
   const bool fits = ex > 0 && ey > 0 && ez > 0 && ex * ey * ez <= BOX_CELLS;
-  const int4 dims2 = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
   const float fmax = __uint_as_float(s_fmax);
+  // w = 1: the vertex order of this box is stored in orec below
+  const int4 lo2 = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, fits && fmax > 0.f ? 1 : 0);
+  const int4 dims2 = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
   if (threadIdx.x == 0) {
     box[0] = lo2;
     box[1] = dims2;
@@ -238,7 +273,17 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
     if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * XFER_THREADS);
   __syncthreads();
   {
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    // the order and counters for the next step's gather at these positions
+    int* wmeta = reinterpret_cast<int*>(orec);
+    unsigned short* widx = reinterpret_cast<unsigned short*>(orec + ORDER_META_INTS * 4);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) widx[i] = order[i];
+    if (threadIdx.x < 32) {
+      wmeta[threadIdx.x] = R.cnt[threadIdx.x];
+      wmeta[32 + threadIdx.x] = R.start[threadIdx.x];
+    }
+    if (threadIdx.x == 0) wmeta[64] = R.most;
+  }
+  {
     const int n = R.cnt[lane], st = R.start[lane];
     for (int w = threadIdx.x >> 5; w < R.most; w += nwarps) {
       if (w >= n) continue;
@@ -257,11 +302,12 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
 template <int GEOM>
 __global__ void __launch_bounds__(XFER_THREADS, 2)
     k_couple(LatticeDev L, float4* g_next, MarkersDev m, BodyDev* __restrict__ bodies, const int2* __restrict__ items,
-             const MarkerGroup* __restrict__ groups, int4* boxes, MeshDev mesh) {
+             const MarkerGroup* __restrict__ groups, int4* boxes, unsigned char* orders, MeshDev mesh) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * 32];
   const int2 it = items[blockIdx.x];  // (body, its transfer group)
-  couple_membrane<GEOM>(L, g_next, m, bodies + it.x, groups[it.y], boxes + 2 * it.y, mesh, smem, red);
+  couple_membrane<GEOM>(L, g_next, m, bodies + it.x, groups[it.y], boxes + 2 * it.y,
+                        orders + (size_t)blockIdx.x * couple_order_stride(mesh.nv), mesh, smem, red);
 }
 
 }  // namespace
@@ -275,8 +321,12 @@ __global__ void __launch_bounds__(XFER_THREADS, 2)
 constexpr int COUPLE_SMEM_MAX = BOX_CELLS * 16 + XFER_GROUP_MAX * 16 + RESIDUE_BYTES;
 
 size_t couple_smem(const MeshDev& mesh) {
-  return (size_t)couple_residues_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;
+  const int res = couple_residues_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;
+  const int gat = (couple_gather_end(mesh.nv) + 15) / 16 * 16;
+  return (size_t)(res > gat ? res : gat);
 }
+
+size_t couple_order_bytes(const MeshDev& mesh) { return (size_t)couple_order_stride(mesh.nv); }
 
 bool couple_fits(const MeshDev& mesh) {
   return mesh.nv >= 1 && mesh.nv <= COUPLE_PER_THREAD * XFER_THREADS && couple_smem(mesh) <= (size_t)COUPLE_SMEM_MAX;
@@ -291,18 +341,19 @@ cudaError_t couple_configure() {
 }
 
 void launch_couple(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* bodies, const int2* items,
-                   int n_items, const MarkerGroup* groups, int4* boxes, const MeshDev& mesh, cudaStream_t st) {
+                   int n_items, const MarkerGroup* groups, int4* boxes, unsigned char* orders, const MeshDev& mesh,
+                   cudaStream_t st) {
   if (n_items == 0) return;
   const size_t smem = couple_smem(mesh);
   switch (L.geometry) {
     case GEOM_PERIODIC:
-      k_couple<GEOM_PERIODIC><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      k_couple<GEOM_PERIODIC><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
     case GEOM_YWALLS:
-      k_couple<GEOM_YWALLS><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      k_couple<GEOM_YWALLS><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
     default:
-      k_couple<GEOM_TUBE><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, mesh);
+      k_couple<GEOM_TUBE><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
   }
 }

@@ -69,6 +69,9 @@ struct ibm_lbm {
   // alternate steps reads the two force-density buffers in turn.
   int2* couple_items = nullptr;   // (body, its transfer group) in group order
   int n_couple = 0;               // > 0: the fused path applies to these markers
+  // per fused body, left by its spreading for the next step's gather: the
+  // vertices' residue counters and order (couple_order_bytes each)
+  unsigned char* couple_order = nullptr;
   float4* gbuf2 = nullptr;        // second force density (allocated on first use)
   bool boxes_valid = false;       // boxes match the markers' current positions (stage interface)
   bool need_zero_F = false;

@@ -36,9 +36,11 @@ void launch_filaments(const MarkersDev& m, const BodyDev* bodies, const int* lis
 
 // couple.cu (membrane suspensions: interpolation, forces and spreading fused per body)
 bool couple_fits(const MeshDev& mesh);
+size_t couple_order_bytes(const MeshDev& mesh);
 cudaError_t couple_configure();
 void launch_couple(const LatticeDev& L, float4* g_next, const MarkersDev& m, BodyDev* bodies, const int2* items,
-                   int n_items, const MarkerGroup* groups, int4* boxes, const MeshDev& mesh, cudaStream_t st);
+                   int n_items, const MarkerGroup* groups, int4* boxes, unsigned char* orders, const MeshDev& mesh,
+                   cudaStream_t st);
 
 // solid.cu
 void launch_solid_half(const MarkersDev& m, double* v, const double* fext, double dt, double gamma, double mass,
