@@ -241,9 +241,12 @@ def couple_traffic(bodies):
         return None
 
 
-def collide_traffic(storage):
-    """DRAM bytes per collide launch from the committed ncu summary, if the
-    kernel source is unchanged since it was taken."""
+def collide_traffic(storage, workload):
+    """DRAM bytes per collide launch of the 256^3 tube from the committed ncu
+    summary, if the kernel source is unchanged since it was taken (other
+    workloads: None, their force-density share differs)."""
+    if not workload.startswith('tube256'):
+        return None
     sha = collide_source_sha()
     p = os.path.join(ROOT, 'profiles', f'collide_tube256_{storage}.md')
     if not os.path.exists(p):
@@ -508,7 +511,7 @@ def run_ours(args):
     step_alg = alg_bytes + M * 72
     step_s = ms_max / 1e3 / args.steps
     collide = dict(kernel='k_collide (fused collide-stream-force)', bound='hbm', achieved=achieved, peak=peak,
-                   unit='GB/s', frac=achieved / peak, traffic=collide_traffic(storage),
+                   unit='GB/s', frac=achieved / peak, traffic=collide_traffic(storage, args.workload),
                    alg_bytes_per_launch=alg_bytes, launch_ms=collide_s * 1e3)
     step = dict(step_alg_bytes=step_alg,
                 step_alg_bytes_formula='N_f*38*s_p + N_touch*24 + M*72 (populations read+written once, force '
