@@ -426,8 +426,9 @@ def fused_path(w, storage):
         return False
     if any(b['kind'] != 0 for b in bodies):
         return False
-    # templates of up to 704 vertices (two per thread of the fused kernel)
-    return sum(b['count'] for b in bodies) == w['X'].shape[1] and w['mesh']['rest_X'].shape[1] <= 704
+    # templates of up to ~938 vertices (the fused kernel's shared memory); the
+    # production-path timing run confirms what the library chose
+    return sum(b['count'] for b in bodies) == w['X'].shape[1] and w['mesh']['rest_X'].shape[1] <= 938
 
 
 def run_ours(args):

@@ -27,8 +27,10 @@
 
 namespace ibm {
 
-// Vertices a thread of the fused kernel advects (templates of up to
-// COUPLE_PER_THREAD * XFER_THREADS vertices take the fused path).
+// Threads of a fused block (16 warps; 64 registers, two blocks per SM) and
+// vertices a thread advects (templates of up to COUPLE_PER_THREAD *
+// COUPLE_THREADS vertices take the fused path).
+constexpr int COUPLE_THREADS = 512;
 constexpr int COUPLE_PER_THREAD = 2;
 
 // Byte offset of the counters in the fused kernel's shared memory.
@@ -99,7 +101,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   double Xo[COUPLE_PER_THREAD][3];
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
+    const int j = threadIdx.x + q * COUPLE_THREADS;
 #pragma unroll
     for (int a = 0; a < 3; ++a) Xo[q][a] = j < nv ? m.X[a * M + G.first + j] : 0.0;
   }
@@ -129,7 +131,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   } else {
 #pragma unroll
     for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-      const int j = threadIdx.x + q * XFER_THREADS;
+      const int j = threadIdx.x + q * COUPLE_THREADS;
       if (j < nv) gather(j);
     }
   }
@@ -138,7 +140,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   const int oa[3] = {o.x, o.y, o.z};
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * XFER_THREADS;
+    const int j = threadIdx.x + q * COUPLE_THREADS;
     if (j >= nv) continue;
     const int k = G.first + j;
     const float4 u = uS[j];
@@ -256,7 +258,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   int l2[COUPLE_PER_THREAD];
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-    const int v = threadIdx.x + q * XFER_THREADS;
+    const int v = threadIdx.x + q * COUPLE_THREADS;
     l2[q] = -1;
     if (v >= nv) continue;
     int c[3];
@@ -270,7 +272,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q)
-    if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * XFER_THREADS);
+    if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * COUPLE_THREADS);
   __syncthreads();
   {
     // the order and counters for the next step's gather at these positions
@@ -300,7 +302,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
 }
 
 template <int GEOM>
-__global__ void __launch_bounds__(XFER_THREADS, 2)
+__global__ void __launch_bounds__(COUPLE_THREADS, 2)
     k_couple(LatticeDev L, float4* g_next, MarkersDev m, BodyDev* __restrict__ bodies, const int2* __restrict__ items,
              const MarkerGroup* __restrict__ groups, int4* boxes, unsigned char* orders, MeshDev mesh) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -313,11 +315,11 @@ __global__ void __launch_bounds__(XFER_THREADS, 2)
 }  // namespace
 
 // Shared memory of the fused kernel for a template of nv vertices: the
-// largest of its three regions (the velocity box; the positions, forces,
-// normals and areas; the positions and forces, the fixed-point box and the
-// vertex order), then the counters. At 642 vertices: 96.5 KiB, two blocks
-// per SM; templates that need more than the interpolation kernel's shared
-// memory take the separate kernels.
+// largest of its regions (the velocity box with the gathered velocities and
+// the gather order; the positions, forces, normals and areas; the positions
+// and forces, the fixed-point box and the vertex order, then the counters).
+// At 642 vertices: 107.3 KiB, two blocks per SM; templates that need more
+// than COUPLE_SMEM_MAX (above ~938 vertices) take the separate kernels.
 constexpr int COUPLE_SMEM_MAX = BOX_CELLS * 16 + XFER_GROUP_MAX * 16 + RESIDUE_BYTES;
 
 size_t couple_smem(const MeshDev& mesh) {
@@ -329,7 +331,7 @@ size_t couple_smem(const MeshDev& mesh) {
 size_t couple_order_bytes(const MeshDev& mesh) { return (size_t)couple_order_stride(mesh.nv); }
 
 bool couple_fits(const MeshDev& mesh) {
-  return mesh.nv >= 1 && mesh.nv <= COUPLE_PER_THREAD * XFER_THREADS && couple_smem(mesh) <= (size_t)COUPLE_SMEM_MAX;
+  return mesh.nv >= 1 && mesh.nv <= COUPLE_PER_THREAD * COUPLE_THREADS && couple_smem(mesh) <= (size_t)COUPLE_SMEM_MAX;
 }
 
 cudaError_t couple_configure() {
@@ -347,13 +349,13 @@ void launch_couple(const LatticeDev& L, float4* g_next, const MarkersDev& m, Bod
   const size_t smem = couple_smem(mesh);
   switch (L.geometry) {
     case GEOM_PERIODIC:
-      k_couple<GEOM_PERIODIC><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
+      k_couple<GEOM_PERIODIC><<<n_items, COUPLE_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
     case GEOM_YWALLS:
-      k_couple<GEOM_YWALLS><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
+      k_couple<GEOM_YWALLS><<<n_items, COUPLE_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
     default:
-      k_couple<GEOM_TUBE><<<n_items, XFER_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
+      k_couple<GEOM_TUBE><<<n_items, COUPLE_THREADS, smem, st>>>(L, g_next, m, bodies, items, groups, boxes, orders, mesh);
       break;
   }
 }
