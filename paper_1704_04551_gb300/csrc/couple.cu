@@ -15,11 +15,13 @@
 // the collision of step n read while other blocks already spread into the
 // one the collision of step n+1 reads.
 //
-// Shared memory (the parts reuse one region): the velocity box and the
-// marker records (part 1); then the vertex positions and forces, the
-// triangle normals and areas (part 2); then the fixed-point box and the
-// marker order (part 3), placed after the positions and forces, which part
-// 3 still reads.
+// Shared memory (the parts reuse one region): the velocity box, the
+// gathered velocities and the gather order (part 1); then the vertex
+// positions and forces, the triangle normals and areas (part 2); then the
+// fixed-point box and the vertex order (part 3), placed after the positions
+// and forces, which part 3 still reads. Part 3 also stores its vertex
+// order in global memory beside the box, for part 1 of the next step,
+// which gathers at the same positions.
 #include "common.cuh"
 #include "forces_body.cuh"
 #include "internal.h"

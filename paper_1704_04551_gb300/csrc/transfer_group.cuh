@@ -26,8 +26,9 @@
 // shared-memory accesses fall in distinct banks (see Residues below).
 // Launches of few groups are bound by the latency of one block's passes:
 // they take larger blocks and four lanes per marker, lane a visiting the
-// stencil's x column a (the *_lanes functions). The block bounds the group's stencils
-// with a box; when the box fits in shared memory (BOX_CELLS cells):
+// stencil's x column a (the *_lanes functions). The block bounds the
+// group's stencils with a box; when the box fits in shared memory
+// (BOX_CELLS cells):
 //   spreading accumulates there in 32-bit fixed point (native integer
 //   shared-memory atomics; the sum does not depend on the order of the
 //   additions) with a scale chosen from the group's largest force so that no
@@ -35,9 +36,9 @@
 //   (one float4 atomic each);
 //   interpolation loads the box of velocities (float4 per cell, so that one
 //   16-byte shared load serves a node) once, with asynchronous copies that
-//   stay in flight while the block sorts its markers, and gathers from
-//   shared memory; the same sweep clears the force density the collision
-//   has consumed.
+//   stay in flight while the block reads its markers' stencil cache, and
+//   gathers from shared memory; the same sweep clears the force density the
+//   collision has consumed.
 // Larger boxes (scattered tracers, very large bodies) fall back to
 // per-marker global float4 atomics / gathers. The box of each group is
 // computed by the spread kernel and reused by the interpolation of the same
