@@ -48,6 +48,13 @@ __host__ __device__ constexpr int couple_residues_offset(int nv, int nt) {
 // float4 and the gather order [nv] ushort.
 __host__ __device__ constexpr int couple_gather_end(int nv) { return BOX_CELLS * 16 + 18 * nv; }
 
+// The counters of the residue sort lie after every region (they are
+// cleared at the start and counted from the end of part 1 on).
+__host__ __device__ constexpr int couple_counters_offset(int nv, int nt) {
+  const int a = couple_residues_offset(nv, nt), b = (couple_gather_end(nv) + 15) / 16 * 16;
+  return a > b ? a : b;
+}
+
 // Per-body record the spreading leaves for the next step's gather: the
 // residue counters (counts [32], starts [32], largest count) of the
 // vertices' first stencil nodes in the box it wrote, then the vertex order.
@@ -85,7 +92,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   unsigned short* oS = reinterpret_cast<unsigned short*>(uS + nv);        // [nv] gather order
   const int* ometa = reinterpret_cast<const int*>(orec);
   const unsigned short* oidx = reinterpret_cast<const unsigned short*>(orec + ORDER_META_INTS * 4);
-  Residues& R = *reinterpret_cast<Residues*>(smem + couple_residues_offset(nv, nt));
+  Residues& R = *reinterpret_cast<Residues*>(smem + couple_counters_offset(nv, nt));
   // origin of the integer parts in shared memory: the first vertex's cell
   // before this step's advection (read before any thread writes the cache)
   const int3 o = make_int3(m.cell[G.first], m.cell[M + G.first], m.cell[2 * M + G.first]);
@@ -100,6 +107,13 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   // markers. The velocities go to shared memory; after a barrier each thread
   // advects its own markers and writes their positions over the box.
   if (in_box) velocity_box_async<GEOM>(L, lo, dims, vbox);
+  // bounds of the new stencils, largest force component, residue counts
+  if (threadIdx.x < 3) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  if (threadIdx.x == 0) s_fmax = 0u;
+  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
   double Xo[COUPLE_PER_THREAD][3];
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
@@ -140,83 +154,84 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   __syncthreads();  // the velocity box is done: the positions go over it
   const MembraneSmem S = MembraneSmem::at(smem, nv, nt);
   const int oa[3] = {o.x, o.y, o.z};
-#pragma unroll
-  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-    const int j = threadIdx.x + q * COUPLE_THREADS;
-    if (j >= nv) continue;
-    const int k = G.first + j;
-    const float4 u = uS[j];
-    m.U[k] = u;
-    const float ua[3] = {u.x, u.y, u.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double Xn = Xo[q][a] + (double)ua[a];
-      m.X[a * M + k] = Xn;
-      const double fl = floor(Xn);
-      const int c = (int)fl;
-      const float f = (float)(Xn - fl);
-      m.cell[a * M + k] = c;
-      m.frac[a * M + k] = f;
-      S.sI[a * nv + j] = (float)(c - oa[a]);
-      S.sR[a * nv + j] = f;
-    }
-  }
-  __syncthreads();
-
-  // ---- 2. membrane forces at X^{n+1} ---------------------------------------
-  membrane_core(B, mesh, S, red);  // ends synchronised
-  const float* sF = reinterpret_cast<const float*>(S.sQ);
-  for (int v = threadIdx.x; v < nv; v += blockDim.x)
-    m.F[G.first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
-
-  // ---- 3. spreading of step n+1 into g_next -------------------------------
-  // stencil box and largest force component of the new positions
-  if (threadIdx.x < 3) {
-    s_lo[threadIdx.x] = INT_MAX;
-    s_hi[threadIdx.x] = INT_MIN;
-  }
-  if (threadIdx.x == 0) s_fmax = 0u;
-  __syncthreads();
   {
     int l[3] = {INT_MAX, INT_MAX, INT_MAX}, h[3] = {INT_MIN, INT_MIN, INT_MIN};
-    float fm = 0.f;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      int c[3];
-      float f[3];
-      smem_cell(S, nv, v, o, c, f);
+#pragma unroll
+    for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
+      const int j = threadIdx.x + q * COUPLE_THREADS;
+      if (j >= nv) continue;
+      const int k = G.first + j;
+      const float4 u = uS[j];
+      m.U[k] = u;
+      const float ua[3] = {u.x, u.y, u.z};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        l[a] = min(l[a], c[a]);
-        h[a] = max(h[a], c[a]);
+        const double Xn = Xo[q][a] + (double)ua[a];
+        m.X[a * M + k] = Xn;
+        const double fl = floor(Xn);
+        const int c = (int)fl;
+        const float f = (float)(Xn - fl);
+        m.cell[a * M + k] = c;
+        m.frac[a * M + k] = f;
+        S.sI[a * nv + j] = (float)(c - oa[a]);
+        S.sR[a * nv + j] = f;
+        l[a] = min(l[a], c);
+        h[a] = max(h[a], c);
       }
-      fm = fmaxf(fm, fmaxf(fabsf(sF[v]), fmaxf(fabsf(sF[nv + v]), fabsf(sF[2 * nv + v]))));
     }
 #pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
+    for (int w = 16; w > 0; w >>= 1)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         l[a] = min(l[a], __shfl_xor_sync(0xffffffffu, l[a], w));
         h[a] = max(h[a], __shfl_xor_sync(0xffffffffu, h[a], w));
       }
-      fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, w));
-    }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         atomicMin(&s_lo[a], l[a]);
         atomicMax(&s_hi[a], h[a]);
       }
-      atomicMax(&s_fmax, __float_as_uint(fm));  // non-negative floats order as their bits
-    }
   }
   __syncthreads();
+  // the stencil box of the new positions (part 3); the vertices are counted
+  // by residue now, while the membrane part runs
   const long long ex = (long long)s_hi[0] - s_lo[0] + 4, ey = (long long)s_hi[1] - s_lo[1] + 4,
                   ez = (long long)s_hi[2] - s_lo[2] + 4;
   const bool fits = ex > 0 && ey > 0 && ez > 0 && ex * ey * ez <= BOX_CELLS;
+  const int4 dims2 = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
+  int l2[COUPLE_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
+    const int v = threadIdx.x + q * COUPLE_THREADS;
+    l2[q] = -1;
+    if (!fits || v >= nv) continue;
+    l2[q] = ((int)S.sI[v] + o.x - s_lo[0]) +
+            dims2.x * (((int)S.sI[nv + v] + o.y - s_lo[1]) + dims2.y * ((int)S.sI[2 * nv + v] + o.z - s_lo[2]));
+    atomicAdd(&R.cnt[l2[q] & 31], 1);
+  }
+
+  // ---- 2. membrane forces at X^{n+1} ---------------------------------------
+  membrane_core(B, mesh, S, red);  // ends synchronised
+  const float* sF = reinterpret_cast<const float*>(S.sQ);
+  {
+    float fm = 0.f;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const float fx = sF[v], fy = sF[nv + v], fz = sF[2 * nv + v];
+      m.F[G.first + v] = make_float4(fx, fy, fz, 0.f);
+      fm = fmaxf(fm, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, w));
+    if (lane == 0) atomicMax(&s_fmax, __float_as_uint(fm));  // non-negative floats order as their bits
+  }
+  if (fits) residue_scan(R);  // warp 0; the counts are complete (barriers in the membrane part)
+  __syncthreads();
+
+  // ---- 3. spreading of step n+1 into g_next -------------------------------
   const float fmax = __uint_as_float(s_fmax);
   // w = 1: the vertex order of this box is stored in orec below
   const int4 lo2 = make_int4(s_lo[0] - 1, s_lo[1] - 1, s_lo[2] - 1, fits && fmax > 0.f ? 1 : 0);
-  const int4 dims2 = make_int4(fits ? (int)ex : 0, fits ? (int)ey : 0, fits ? (int)ez : 0, fits ? 1 : 0);
   if (threadIdx.x == 0) {
     box[0] = lo2;
     box[1] = dims2;
@@ -255,23 +270,6 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   const int vol = dims2.x * dims2.y * dims2.z;
   const float Sc = fminf(33554432.0f, 8589934592.0f / (float)nv) / fmax;  // as in spread_group
   for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x) ibox[i] = 0;
-  if (threadIdx.x < 32) R.cnt[threadIdx.x] = 0;
-  __syncthreads();
-  int l2[COUPLE_PER_THREAD];
-#pragma unroll
-  for (int q = 0; q < COUPLE_PER_THREAD; ++q) {
-    const int v = threadIdx.x + q * COUPLE_THREADS;
-    l2[q] = -1;
-    if (v >= nv) continue;
-    int c[3];
-    float f[3];
-    smem_cell(S, nv, v, o, c, f);
-    l2[q] = (c[0] - 1 - lo2.x) + dims2.x * ((c[1] - 1 - lo2.y) + dims2.y * (c[2] - 1 - lo2.z));
-    atomicAdd(&R.cnt[l2[q] & 31], 1);
-  }
-  __syncthreads();
-  residue_scan(R);
-  __syncthreads();
 #pragma unroll
   for (int q = 0; q < COUPLE_PER_THREAD; ++q)
     if (l2[q] >= 0) order[atomicAdd(&R.cur[l2[q] & 31], 1)] = (unsigned short)(threadIdx.x + q * COUPLE_THREADS);
@@ -325,9 +323,7 @@ __global__ void __launch_bounds__(COUPLE_THREADS, 2)
 constexpr int COUPLE_SMEM_MAX = BOX_CELLS * 16 + XFER_GROUP_MAX * 16 + RESIDUE_BYTES;
 
 size_t couple_smem(const MeshDev& mesh) {
-  const int res = couple_residues_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;
-  const int gat = (couple_gather_end(mesh.nv) + 15) / 16 * 16;
-  return (size_t)(res > gat ? res : gat);
+  return (size_t)couple_counters_offset(mesh.nv, mesh.nt) + RESIDUE_BYTES;
 }
 
 size_t couple_order_bytes(const MeshDev& mesh) { return (size_t)couple_order_stride(mesh.nv); }
