@@ -212,12 +212,11 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
   }
 
   // ---- 2. membrane forces at X^{n+1} ---------------------------------------
-  membrane_core(B, mesh, S, red);  // ends synchronised
-  const float* sF = reinterpret_cast<const float*>(S.sQ);
+  const ForceSums sF = membrane_core(B, mesh, S, red);  // ends synchronised
   {
     float fm = 0.f;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      const float fx = sF[v], fy = sF[nv + v], fz = sF[2 * nv + v];
+      const float fx = sF(v), fy = sF(nv + v), fz = sF(2 * nv + v);
       m.F[G.first + v] = make_float4(fx, fy, fz, 0.f);
       fm = fmaxf(fm, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
     }
@@ -258,7 +257,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
       axis_weights(f[2], st.wz);
       mark_tiles<GEOM>(Ln, st.bx, st.by, st.bz, active);
       if (active && fmax > 0.f)
-        scatter_global<GEOM>(Ln, st, make_float4(sF[vv], sF[nv + vv], sF[2 * nv + vv], 0.f));
+        scatter_global<GEOM>(Ln, st, make_float4(sF(vv), sF(nv + vv), sF(2 * nv + vv), 0.f));
     }
     return;
   }
@@ -294,7 +293,7 @@ __device__ __forceinline__ void couple_membrane(const LatticeDev& L, float4* g_n
       float f[3];
       smem_cell(S, nv, v, o, c, f);
       const int li0 = (c[0] - 1 - lo2.x) + dims2.x * ((c[1] - 1 - lo2.y) + dims2.y * (c[2] - 1 - lo2.z));
-      scatter_marker(ibox, vol, dims2, li0, f[0], f[1], f[2], sF[v] * Sc, sF[nv + v] * Sc, sF[2 * nv + v] * Sc);
+      scatter_marker(ibox, vol, dims2, li0, f[0], f[1], f[2], sF(v) * Sc, sF(nv + v) * Sc, sF(2 * nv + v) * Sc);
     }
   }
   __syncthreads();

@@ -98,7 +98,19 @@ struct MembraneSmem {
   }
 };
 
-__device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S, double* red);
+// The per-vertex force sums membrane_core leaves in S.sQ [3][nv]: fixed-point
+// integers in units of `unit`, or float bits after the float redo.
+struct ForceSums {
+  const int* q;
+  bool is_float;
+  float unit;
+  __device__ __forceinline__ float operator()(int i) const {
+    return is_float ? __int_as_float(q[i]) : (float)q[i] * unit;
+  }
+};
+
+__device__ __forceinline__ ForceSums membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S,
+                                                   double* red);
 
 // Membrane forces of one body by the whole thread block. smem: [9 nv + 4 nt]
 // words (positions as floor + fraction, force sums, normals, areas);
@@ -127,16 +139,16 @@ __device__ __forceinline__ void membrane_block(const MarkersDev& m, BodyDev* Bp,
     }
   }
   __syncthreads();
-  membrane_core(Bp, mesh, S, red);
-  const float* sF = reinterpret_cast<const float*>(S.sQ);
-  for (int v = threadIdx.x; v < nv; v += blockDim.x)
-    m.F[first + v] = make_float4(sF[v], sF[nv + v], sF[2 * nv + v], 0.f);
+  const ForceSums F = membrane_core(Bp, mesh, S, red);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) m.F[first + v] = make_float4(F(v), F(nv + v), F(2 * nv + v), 0.f);
 }
 
 // Forces of one membrane whose positions are in S.sI / S.sR (the caller has
-// synchronised after writing them): S.sQ receives the forces as floats
-// [3][nv], Bp->qmax the scale for the next step; ends synchronised.
-__device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S, double* red) {
+// synchronised after writing them): S.sQ receives the per-vertex sums
+// [3][nv] (read through the returned ForceSums), Bp->qmax the scale for the
+// next step; ends synchronised.
+__device__ __forceinline__ ForceSums membrane_core(BodyDev* Bp, const MeshDev& mesh, const MembraneSmem& S,
+                                                   double* red) {
   const Topo T = topo_at(mesh.packed, mesh);
   const int nv = mesh.nv, nt = mesh.nt, ne = mesh.ne;
   const float kBT_p = Bp->kBT_p, k_b = Bp->k_b, k_l = Bp->k_l, k_g = Bp->k_g, k_v = Bp->k_v;
@@ -278,10 +290,9 @@ __device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, 
     pass_b([&](int v, float3 f) {
       const float c = fmaxf(fabsf(f.x), fmaxf(fabsf(f.y), fabsf(f.z)));
       qmax = fmaxf(qmax, c);
-      if (!(c * Sq <= mesh.qcap)) {  // also catches non-finite values
-        over = true;
-        return;
-      }
+      // a contribution above the headroom (or not finite) sends the block to
+      // the float redo, which discards these sums: no branch here
+      over |= !(c * Sq <= mesh.qcap);
       atomicAdd(sQ + v, __float2int_rn(f.x * Sq));
       atomicAdd(sQ + nv + v, __float2int_rn(f.y * Sq));
       atomicAdd(sQ + 2 * nv + v, __float2int_rn(f.z * Sq));
@@ -302,16 +313,16 @@ __device__ __forceinline__ void membrane_core(BodyDev* Bp, const MeshDev& mesh, 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
   if ((threadIdx.x & 31) == 0) atomicMax(&s_qmax, __float_as_uint(qmax));  // non-negative floats order as their bits
-  __syncthreads();
-  if (!fallback) {
-    const float inv = 1.0f / Sq;
-    for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) sQ[i] = __float_as_int((float)sQ[i] * inv);
-  }
+  __syncthreads();  // the sums and s_qmax are complete
   if (threadIdx.x == 0) {
     const float q = __uint_as_float(s_qmax);
     Bp->qmax = isfinite(q) ? q : 0.f;
   }
-  __syncthreads();
+  ForceSums F;
+  F.q = sQ;
+  F.is_float = fallback;
+  F.unit = fallback ? 0.f : 1.0f / Sq;
+  return F;
 }
 
 // Filament forces of one bead chain (polymer particles, Sec. 2.2) by the
