@@ -1099,13 +1099,15 @@ static int set_markers_into(ibm_lbm_t* h, const ibm_lbm_mesh* mesh, int32_t n_bo
     if (fused) {
       std::unordered_map<int, int> body_of_first;
       for (int b = 0; b < n_bodies; ++b) body_of_first[(int)bodies[b].first] = b;
+      // items[g] = (body, g) for every group g in order: the fused kernel's
+      // block g reads group g and its box directly
       std::vector<int2> items;
       for (size_t g = 0; g < groups.size() && fused; ++g) {
         auto it = body_of_first.find(groups[g].first);
         if (it == body_of_first.end() || groups[g].count != (int)bodies[it->second].count) fused = false;
         else items.push_back(make_int2(it->second, (int)g));
       }
-      if (fused && (int)items.size() == n_bodies) {
+      if (fused && (int)items.size() == n_bodies && items.size() == groups.size()) {
         if ((rc = upload<int2>(h, h->marker_mem, &h->couple_items, items.data(), items.size()))) return rc;
         h->couple_order = (unsigned char*)dalloc(h, h->marker_mem, couple_order_bytes(h->mesh) * items.size());
         if (!h->couple_order) return fail(h, IBM_LBM_E_NOMEM, "device allocation failed");

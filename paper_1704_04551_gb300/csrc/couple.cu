@@ -306,9 +306,11 @@ __global__ void __launch_bounds__(COUPLE_THREADS, 2)
              const MarkerGroup* __restrict__ groups, int4* boxes, unsigned char* orders, MeshDev mesh) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * 32];
-  const int2 it = items[blockIdx.x];  // (body, its transfer group)
-  couple_membrane<GEOM>(L, g_next, m, bodies + it.x, groups[it.y], boxes + 2 * it.y,
-                        orders + (size_t)blockIdx.x * couple_order_stride(mesh.nv), mesh, smem, red);
+  // items[b] = (body, group b): the items follow the group order, so the
+  // group and its box are read without waiting for the item
+  const int b = blockIdx.x;
+  couple_membrane<GEOM>(L, g_next, m, bodies + items[b].x, groups[b], boxes + 2 * b,
+                        orders + (size_t)b * couple_order_stride(mesh.nv), mesh, smem, red);
 }
 
 }  // namespace
