@@ -43,7 +43,18 @@ __global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_col
   const int r = rb * blockDim.y + threadIdx.y;
   const int x = xb * blockDim.x + threadIdx.x;
   if (r >= n_rows || x >= L.nx) return;
-  collide_cell<S, ODD, GEOM, DENSE, IDX32>(L, rows[r], x);
+  const RowInfo R = rows[r];
+  // In the neighbour-addressed (odd) step, rows without solid neighbours
+  // (all but a ring of rows along walls) skip the bounce-back tests; a warp
+  // lies in one row, so the branch is uniform. (The even step reads and
+  // writes its own cell only: a second copy there only cost registers.)
+  if constexpr (ODD == 1 && GEOM != GEOM_PERIODIC) {
+    if (R.smask == 0) {
+      collide_cell<S, ODD, GEOM, DENSE, IDX32, true>(L, R, x);
+      return;
+    }
+  }
+  collide_cell<S, ODD, GEOM, DENSE, IDX32>(L, R, x);
 }
 
 // Equilibrium initialisation from the moments in uw (ux, uy, uz, rho - 1).

@@ -180,8 +180,11 @@ __device__ __forceinline__ float relax_cell(const LatticeDev& L, float d[Q], int
 // IDX32: element offsets of the neighbour-addressed (odd) step computed in
 // 32 bits, valid while 19 N < 2^32 (fewer integer instructions than 64-bit
 // address arithmetic per population; the odd step is issue-bound).
-template <int S, int ODD, int GEOM, bool DENSE, bool IDX32 = false>
+// INTERIOR: the row's y/z neighbour rows are all fluid (R.smask == 0), so
+// no population is bounced back and the solid tests drop out.
+template <int S, int ODD, int GEOM, bool DENSE, bool IDX32 = false, bool INTERIOR = false>
 __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo& R, int x) {
+  constexpr bool WALLS = GEOM != GEOM_PERIODIC && !INTERIOR;  // solid neighbours possible
   using P = Pop<S>;
   using T = typename P::T;
   const int idx = R.base + x;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
   float d[Q];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
-    if (!ODD || j == 0 || ((GEOM != GEOM_PERIODIC) && nb_solid(c, j, -1)))
+    if (!ODD || j == 0 || (WALLS && nb_solid(c, j, -1)))
       d[j] = P::ld_raw(elem(j, idx));
     else
       d[j] = P::ld_raw(elem(opp(j), idx + nb_off(c, j, -1)));
@@ -225,7 +228,7 @@ __device__ __forceinline__ void collide_cell(const LatticeDev& L, const RowInfo&
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     float v = d[i];
-    const bool sol = (GEOM != GEOM_PERIODIC) && i != 0 && nb_solid(c, i, +1);
+    const bool sol = WALLS && i != 0 && nb_solid(c, i, +1);
     if (GEOM == GEOM_YWALLS && sol && cx(i) != 0) {
       // stored into slot opp(i): the half-precision scale of that slot
       const float uw = (c.y + cy(i) < 0) ? L.wall_u0 : L.wall_u1;
