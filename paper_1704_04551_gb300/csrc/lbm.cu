@@ -29,15 +29,22 @@ namespace ibm {
 // them are solid) come from the precomputed row table, so a thread does no
 // integer division and no geometry arithmetic.
 constexpr int COLLIDE_THREADS = 128;
+// Resident blocks per SM the register budget is sized for: 8 (64 registers)
+// for FP32 storage; 10 (48 registers) for the half-precision formats, whose
+// cells move half the bytes, so that more of them are in flight (FP16 even
+// step 244 -> 228 us at 256^3).
 #ifndef IBM_COLLIDE_MIN_BLOCKS
-#define IBM_COLLIDE_MIN_BLOCKS 8  // resident blocks per SM the register budget is sized for
+#define IBM_COLLIDE_MIN_BLOCKS 8
+#endif
+#ifndef IBM_COLLIDE_MIN_BLOCKS_HALF
+#define IBM_COLLIDE_MIN_BLOCKS_HALF 10
 #endif
 
 // The grid is one-dimensional (a row count above 65535 blocks does not fit
 // the y dimension): block b covers x chunk b % nxb of row block b / nxb,
 // x chunks of a row consecutive.
 template <int S, int ODD, int GEOM, bool DENSE, bool IDX32>
-__global__ void __launch_bounds__(COLLIDE_THREADS, IBM_COLLIDE_MIN_BLOCKS) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
+__global__ void __launch_bounds__(COLLIDE_THREADS, S == STORE_F32 ? IBM_COLLIDE_MIN_BLOCKS : IBM_COLLIDE_MIN_BLOCKS_HALF) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
                                                                 int n_rows, int nxb) {
   const int rb = blockIdx.x / nxb, xb = blockIdx.x - rb * nxb;
   const int r = rb * blockDim.y + threadIdx.y;
