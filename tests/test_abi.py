@@ -46,6 +46,9 @@ def test_binding_signatures_load(libpath):
     cfg.tau = 0.4
     assert L.ibm_lbm_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == binding.E_ARG
     assert L.ibm_lbm_destroy(None) == 0
+    # timing controls on a NULL handle are argument errors, not crashes
+    assert L.ibm_lbm_set_timing(None, 4) == binding.E_ARG
+    assert L.ibm_lbm_set_timing_fused(None, 1) == binding.E_ARG
 
 
 def test_calls_without_a_device_fail_with_a_status(libpath):
