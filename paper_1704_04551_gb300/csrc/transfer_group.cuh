@@ -35,8 +35,7 @@
 //   cell can overflow, then adds the box's nonzero cells to global memory
 //   (one float4 atomic each);
 //   interpolation loads the box of velocities (float4 per cell, so that one
-//   16-byte shared load serves a node) once, with asynchronous copies that
-//   stay in flight while the block reads its markers' stencil cache, and
+//   16-byte shared load serves a node) once, with asynchronous copies, and
 //   gathers from shared memory; the same sweep clears the force density the
 //   collision has consumed.
 // Larger boxes (scattered tracers, very large bodies) fall back to
