@@ -29,22 +29,22 @@ namespace ibm {
 // them are solid) come from the precomputed row table, so a thread does no
 // integer division and no geometry arithmetic.
 constexpr int COLLIDE_THREADS = 128;
-// Resident blocks per SM the register budget is sized for: 8 (64 registers)
-// for FP32 storage; 10 (48 registers) for the half-precision formats, whose
-// cells move half the bytes, so that more of them are in flight (FP16 even
-// step 244 -> 228 us at 256^3).
-#ifndef IBM_COLLIDE_MIN_BLOCKS
-#define IBM_COLLIDE_MIN_BLOCKS 8
-#endif
-#ifndef IBM_COLLIDE_MIN_BLOCKS_HALF
-#define IBM_COLLIDE_MIN_BLOCKS_HALF 10
-#endif
+// Resident blocks per SM the register budget is sized for (more blocks,
+// more loads in flight; fewer registers): measured best at 256^3 with 10
+// (48 registers) for the local even step, 9 (56 registers) for the
+// neighbour-addressed odd step in FP32 and 10 for it in the half-precision
+// formats. FP32: even 324 -> 316 us, odd 356 -> 331 us against 8 blocks (64
+// registers); FP16 even 244 -> 228 us.
+template <int S, int ODD>
+constexpr int collide_min_blocks() {
+  return (S == STORE_F32 && ODD) ? 9 : 10;
+}
 
 // The grid is one-dimensional (a row count above 65535 blocks does not fit
 // the y dimension): block b covers x chunk b % nxb of row block b / nxb,
 // x chunks of a row consecutive.
 template <int S, int ODD, int GEOM, bool DENSE, bool IDX32>
-__global__ void __launch_bounds__(COLLIDE_THREADS, S == STORE_F32 ? IBM_COLLIDE_MIN_BLOCKS : IBM_COLLIDE_MIN_BLOCKS_HALF) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
+__global__ void __launch_bounds__(COLLIDE_THREADS, (collide_min_blocks<S, ODD>())) k_collide(LatticeDev L, const RowInfo* __restrict__ rows,
                                                                 int n_rows, int nxb) {
   const int rb = blockIdx.x / nxb, xb = blockIdx.x - rb * nxb;
   const int r = rb * blockDim.y + threadIdx.y;
