@@ -175,8 +175,10 @@ __global__ void __launch_bounds__(LANE_THREADS, 1) k_interpolate_bl(const CaseDe
 // chunk boundaries and every chunk has an even number of steps, so all
 // running cases share the AA parity of a step and it is a template argument;
 // rows are grouped by geometry, one launch per geometry present.
+// 10 resident blocks per SM for the even step, 9 for the odd one, as for the
+// single-lattice collide (64-case stream: 17,610 -> 18,150 MLUPS against 6).
 template <int ODD, int GEOM>
-__global__ void __launch_bounds__(SERVE_COLLIDE_TX * SERVE_COLLIDE_TY, 6)
+__global__ void __launch_bounds__(SERVE_COLLIDE_TX * SERVE_COLLIDE_TY, ODD ? 9 : 10)
     k_collide_b(const CaseDev* cases, const Item* items, int n_items, int nxb) {
   const int ib = blockIdx.x / nxb, xb = blockIdx.x - ib * nxb;  // one-dimensional grid, x chunks fastest
   const int item = ib * blockDim.y + threadIdx.y;
