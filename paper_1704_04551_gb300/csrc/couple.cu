@@ -35,7 +35,9 @@ namespace ibm {
 constexpr int COUPLE_THREADS = 512;
 constexpr int COUPLE_PER_THREAD = 2;
 
-// Byte offset of the counters in the fused kernel's shared memory.
+// End (bytes, rounded to 16) of the largest of the parts' regions: the
+// velocity box; the membrane arrays; the positions, forces, fixed-point box
+// and vertex order.
 __host__ __device__ constexpr int couple_residues_offset(int nv, int nt) {
   const int box = BOX_CELLS * 16;
   const int forces = 36 * nv + 16 * nt;
